@@ -1,0 +1,64 @@
+"""The named synthetic workloads, with their sizes and seeds.
+
+Load-factor counts use floor(alpha * m * b).  All key streams are
+splitmix64 outputs of one seed, so positives and negatives taken from
+disjoint index ranges of the same seed are disjoint sets.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+
+def lf_count(m: int, b: int, alpha: float) -> int:
+    """floor(alpha * m * b), computed exactly for the decimal alphas used."""
+    num = round(alpha * 10**6)
+    return (m * b * num) // 10**6
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    m: int              # buckets
+    f: int              # fingerprint bits
+    b: int              # slots per bucket
+    max_evictions: int
+    key_seed: int
+    alphas: tuple       # load factors the insert phase passes through
+    n_queries: int
+    query_pos_seed: int
+    n_deletes: int
+
+    @property
+    def n_insert(self) -> int:
+        return lf_count(self.m, self.b, self.alphas[-1])
+
+    @property
+    def table_bytes(self) -> int:
+        return self.m * self.b * self.f // 8
+
+    def insert_segments(self):
+        """[(lo, hi)] key-index ranges filling 0 -> alphas[0] -> ... ."""
+        out, lo = [], 0
+        for a in self.alphas:
+            hi = lf_count(self.m, self.b, a)
+            out.append((lo, hi))
+            lo = hi
+        return out
+
+    def ops_per_step(self) -> int:
+        return self.n_insert + self.n_queries + self.n_deletes
+
+
+# Single filter, 2^18 buckets x 4 slots, 16-bit fingerprints (2 MiB table):
+# insert floor(0.95 * 2^20) keys, query them plus 2^20 disjoint negatives,
+# delete the first half and query everything again.
+SINGLE = Workload(name="single_2^18x4_f16", m=1 << 18, f=16, b=4,
+                  max_evictions=500, key_seed=1, alphas=(0.95,),
+                  n_queries=0, query_pos_seed=0, n_deletes=0)
+
+# Single large filter, 2^28 buckets x 4 slots, 16-bit fingerprints (2 GiB):
+# fill through load factors 0.5 / 0.8 / 0.95, then 2^30 queries at a 50%
+# positive mix, then delete 2^28 inserted keys.
+LARGE = Workload(name="large_2^28x4_f16_lf0.95", m=1 << 28, f=16, b=4,
+                 max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
+                 n_queries=1 << 30, query_pos_seed=12, n_deletes=1 << 28)
