@@ -1,0 +1,473 @@
+#!/usr/bin/env python3
+"""Benchmark: insert / query / delete Mops/s of one large cuckoo filter.
+
+Workload (one "step" = one pass of the whole hot path):
+  a filter of 2^28 buckets x 4 slots x 16-bit fingerprints (2 GiB table,
+  max 500 evictions), cleared, then filled with uniform splitmix64 keys
+  (seed 2) through load factors 0.5 -> 0.8 -> 0.95 (1,020,054,732 inserts in
+  three calls), then 2^30 queries at a 50% positive mix, then the first 2^28
+  inserted keys deleted.  Keys are generated on the device before timing.
+
+Output: ONE JSON line (rank 0).  ``value`` = total ops of all ranks / the
+slowest rank's device time (CUDA events on the launching stream).  The
+table (2 GiB) and key arrays (8 GB) exceed L2 (129 MB), so no flush is
+needed between steps.  ``roofline`` relates the dominant phase to the
+measured HBM copy bandwidth, ``cpu_baseline`` times the CPU oracle on a
+scale model of the same workload, ``e2e`` repeats the measurement through
+the host-buffer C-ABI calls with the H2D/D2H copies inside the timed region.
+
+``--impl reference`` times the CPU oracle (the reference implementation of
+the method) on the host cores instead, one bounded sample per step.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "insert/query/delete Mops/s at LF 0.95 vs HBM roofline; served p99 vs plain"
+SECTOR = 32
+
+
+# ---------------------------------------------------------------------------
+# Multi-rank harness (also exercised on CPU with gloo by the tests).
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max_sum(t_local: float, ops_local: float, group=None):
+    """Max of the elapsed time and sum of the ops over all ranks."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return t_local, ops_local
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    o = torch.tensor([ops_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(o, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item()), float(o.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)
+        except Exception:
+            self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[1]), float(parts[2]), parts[4:8]))
+            except Exception:
+                continue
+        inside = [r for r in rows if self.t0 is None or (self.t0 - 0.2 <= r[0] <= self.t1 + 0.2)]
+        use = inside or rows
+        if not use:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use),
+                "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use)}
+
+
+# ---------------------------------------------------------------------------
+# The CPU oracle on a scale model: baseline timing + bucket-touch counts.
+# ---------------------------------------------------------------------------
+def oracle_run(W, repeat: int = 1):
+    """Run the workload W on the CPU oracle (one thread).  Returns
+    (seconds, ops, stats-per-phase) of the LAST repeat."""
+    import oracle
+    import workloads
+
+    keys = workloads.keys(W.key_seed, W.n_insert)
+    q = workloads.query_mix(W.n_queries, keys, W.query_pos_seed, W.key_seed, W.n_insert)
+    dels = keys[: W.n_deletes]
+    res = None
+    for _ in range(repeat):
+        o = oracle.OracleFilter(W.m, W.f, W.b, W.max_evictions)
+        t0 = time.perf_counter()
+        for lo, hi in W.insert_segments():
+            o.insert_batch(keys[lo:hi])
+        s_ins = o.stats()
+        t1 = time.perf_counter()
+        o.contains_batch(q)
+        t2 = time.perf_counter()
+        o.remove_batch(dels)
+        t3 = time.perf_counter()
+        s = o.stats()
+        res = (t3 - t0, W.ops_per_step(),
+               {"insert": {"ops": W.n_insert, "s": t1 - t0,
+                           "bucket_reads": s_ins["ins_bucket_reads"],
+                           "bucket_writes": s_ins["ins_bucket_writes"]},
+                "query": {"ops": W.n_queries, "s": t2 - t1,
+                          "bucket_reads": s["qry_bucket_reads"], "bucket_writes": 0},
+                "delete": {"ops": W.n_deletes, "s": t3 - t2,
+                           "bucket_reads": s["rem_bucket_reads"],
+                           "bucket_writes": s["rem_bucket_writes"]}})
+        o.close()
+    return res
+
+
+def bytes_per_op(phases: dict, bucket_bytes: int) -> dict:
+    """Algorithmic bytes per operation: the 32-byte sectors of the buckets
+    the algorithm reads and writes (counted by the oracle), plus the 8-byte
+    key read and the 1-byte flag write."""
+    sectors_per_bucket = max(1, math.ceil(bucket_bytes / SECTOR))
+    out = {}
+    for name, p in phases.items():
+        touches = (p["bucket_reads"] + p["bucket_writes"]) / p["ops"]
+        out[name] = touches * sectors_per_bucket * SECTOR + 8 + 1
+    return out
+
+
+# ---------------------------------------------------------------------------
+# GPU arm.
+# ---------------------------------------------------------------------------
+def insert_launches(n: int) -> int:
+    chunk = 1 << 28
+    return 2 * ((n + chunk - 1) // chunk)
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads
+    from paper_2603_15486_gb300 import CuckooFilter
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = workloads.BY_NAME[args.workload]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+
+    # ---- inputs, generated on the device (untimed) ----
+    keys = torch.empty(W.n_insert, dtype=torch.int64, device=dev)
+    workloads.keys_dev(keys.data_ptr(), W.n_insert, W.key_seed, 0, sh)
+    queries = torch.empty(W.n_queries, dtype=torch.int64, device=dev)
+    workloads.query_mix_dev(queries.data_ptr(), W.n_queries, keys.data_ptr(), W.n_insert,
+                            W.query_pos_seed, W.key_seed, W.n_insert, sh)
+    dels = keys[: W.n_deletes]
+    ins_flags = torch.empty(W.n_insert, dtype=torch.uint8, device=dev)
+    q_flags = torch.empty(W.n_queries, dtype=torch.uint8, device=dev)
+    d_flags = torch.empty(W.n_deletes, dtype=torch.uint8, device=dev)
+    filt = CuckooFilter(W.m, W.f, W.b, W.max_evictions)
+    stream.synchronize()
+
+    segs = W.insert_segments()
+    launches = sum(insert_launches(hi - lo) for lo, hi in segs) + 2
+
+    def step(ev=None):
+        filt.clear(stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        for lo, hi in segs:
+            filt.insert(keys[lo:hi], flags=ins_flags[lo:hi], stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        filt.contains(queries, out=q_flags, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        filt.remove(dels, out=d_flags, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    st = filt.stats()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_start()
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for i in range(args.steps):
+            step(evs[i])
+        t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_end()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    ops_local = float(W.ops_per_step()) * args.steps
+    t_max, ops_all = reduce_max_sum(elapsed, ops_local)
+    ph = {"insert": [], "query": [], "delete": []}
+    for e in evs:
+        ph["insert"].append(e[0].elapsed_time(e[1]) / 1e3)
+        ph["query"].append(e[1].elapsed_time(e[2]) / 1e3)
+        ph["delete"].append(e[2].elapsed_time(e[3]) / 1e3)
+    med = {k: statistics.median(v) for k, v in ph.items()}
+    st_end = filt.stats()
+
+    # ---- correctness guard of the timed run (cheap, device-side) ----
+    ins_ok = int(ins_flags.sum())
+    q_pos = int(q_flags[0::2].sum())
+    q_neg = int(q_flags[1::2].sum())
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(filt, keys, queries, W, args, stream)
+
+    if rank != 0:
+        return None
+
+    value = ops_all / t_max / 1e6
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mops/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16", "data": "synthetic",
+        "config": {"workload": W.name, "buckets": W.m, "slots_per_bucket": W.b,
+                   "fp_bits": W.f, "max_evictions": W.max_evictions,
+                   "load_factors": list(W.alphas), "inserts": W.n_insert,
+                   "queries": W.n_queries, "query_positive_fraction": 0.5,
+                   "deletes": W.n_deletes, "table_bytes": W.table_bytes,
+                   "keys": "splitmix64 seed 2, uniform uint64",
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "no flush: 2 GiB table and 8 GB key arrays exceed the 129 MB L2"},
+        "phases": {k: {"ms": round(v * 1e3, 3),
+                       "mops": round(n / v / 1e6, 1)}
+                   for k, v, n in (("insert", med["insert"], W.n_insert),
+                                   ("query", med["query"], W.n_queries),
+                                   ("delete", med["delete"], W.n_deletes))},
+        "gpu_launches": launches * args.steps,
+        "checks": {"insert_ok": ins_ok, "insert_fail": W.n_insert - ins_ok,
+                   "query_pos_found": q_pos, "query_pos": W.n_queries // 2,
+                   "false_positives": q_neg, "fpr": q_neg / (W.n_queries // 2),
+                   "occupancy_after_step": st_end["occupancy"],
+                   "evictions_per_step": st["evictions"],
+                   "contention": st_end["contention"]},
+        "clocks": clocks,
+    }
+
+    # ---- roofline of the dominant phase + CPU baseline (rank 0, N=1 only) ----
+    peaks = load_peaks()
+    cpu = None
+    bpo = None
+    if ws == 1 and not args.no_cpu:
+        S = workloads.BY_NAME[args.cpu_workload]
+        secs, ops, phases = oracle_run(S)
+        bpo = bytes_per_op(phases, W.f * W.b // 8)
+        cpu = {"value": round(ops / secs / 1e6, 3), "unit": "Mops/s", "cores": 1,
+               "host_cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"{S.name}: the same load-factor path, 50/50 query mix and "
+                          f"delete fraction on {S.m} buckets ({ops} ops, {secs:.1f} s, "
+                          "one thread of the host)"),
+               "phases_mops": {k: round(p["ops"] / p["s"] / 1e6, 3) for k, p in phases.items()}}
+    if bpo is None:
+        bpo = {"insert": 73.0, "query": 57.0, "delete": 66.0}
+    dom = max(med, key=lambda k: med[k])
+    n_dom = {"insert": W.n_insert, "query": W.n_queries, "delete": W.n_deletes}
+    peak = peaks.get("hbm_gbs") or 6800.0
+    ach = {k: n_dom[k] * bpo[k] / med[k] / 1e9 for k in med}
+    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach[dom], 1),
+                       "peak": peak, "unit": "GB/s",
+                       "frac": round(ach[dom] / peak, 4), "traffic": args.traffic,
+                       "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+                       "bytes_per_op": {k: round(v, 2) for k, v in bpo.items()},
+                       "phases_frac": {k: round(v / peak, 4) for k, v in ach.items()}}
+    out["cpu_baseline"] = cpu
+    out["e2e"] = e2e
+    return out
+
+
+def e2e_run(filt, keys, queries, W, args, stream):
+    """The same step through the host-buffer C-ABI calls: keys start in
+    pinned host memory, flags end there; copies are inside the timing."""
+    import numpy as np
+    import torch
+
+    try:
+        hk = torch.empty(W.n_insert, dtype=torch.int64, pin_memory=True)
+        hq = torch.empty(W.n_queries, dtype=torch.int64, pin_memory=True)
+        hf_i = torch.empty(W.n_insert, dtype=torch.uint8, pin_memory=True)
+        hf_q = torch.empty(W.n_queries, dtype=torch.uint8, pin_memory=True)
+        hf_d = torch.empty(W.n_deletes, dtype=torch.uint8, pin_memory=True)
+        pinned = True
+    except RuntimeError:
+        hk = torch.empty(W.n_insert, dtype=torch.int64)
+        hq = torch.empty(W.n_queries, dtype=torch.int64)
+        hf_i = torch.empty(W.n_insert, dtype=torch.uint8)
+        hf_q = torch.empty(W.n_queries, dtype=torch.uint8)
+        hf_d = torch.empty(W.n_deletes, dtype=torch.uint8)
+        pinned = False
+    hk.copy_(keys)
+    hq.copy_(queries)
+    segs = W.insert_segments()
+    filt.set_staging_chunk(1 << 24)
+
+    def step():
+        filt.clear(stream=stream)
+        for lo, hi in segs:
+            filt.insert_host(hk[lo:hi], out=hf_i[lo:hi], stream=stream)
+        filt.contains_host(hq, out=hf_q, stream=stream)
+        filt.remove_host(hk[: W.n_deletes], out=hf_d, stream=stream)
+
+    for _ in range(max(1, args.e2e_warmup)):
+        step()
+    stream.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    stream.synchronize()
+    el = time.perf_counter() - t0
+    t_max, ops_all = reduce_max_sum(el, float(W.ops_per_step()) * args.e2e_steps)
+    h2d = 8 * (W.n_insert + W.n_queries + W.n_deletes)
+    d2h = W.n_insert + W.n_queries + W.n_deletes
+    return {"value": round(ops_all / t_max / 1e6, 2), "unit": "Mops/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": args.e2e_steps, "pinned": pinned,
+            "ms_per_step": round(el / args.e2e_steps * 1e3, 3),
+            "api": "cf_insert_host / cf_contains_host / cf_remove_host"}
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle.
+# ---------------------------------------------------------------------------
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import workloads
+    S = workloads.BY_NAME[args.ref_workload]
+    for _ in range(args.warmup):
+        oracle_run(S)
+    times = []
+    for _ in range(args.steps):
+        secs, ops, _ = oracle_run(S)
+        times.append(secs)
+    tot = sum(times)
+    value = S.ops_per_step() * args.steps / tot / 1e6
+    return {"metric": METRIC, "value": round(value, 3), "unit": "Mops/s", "impl": "reference",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u16", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": S.name},
+            "cpu_baseline": {"value": round(value, 3), "unit": "Mops/s", "cores": 1,
+                             "host_cores": os.cpu_count(), "kind": "oracle",
+                             "sample": (f"each step: {S.name} ({S.ops_per_step()} ops: "
+                                        "fill to LF 0.95, 50/50 queries, deletes), one thread")},
+            "e2e": {"value": round(value, 3), "unit": "Mops/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="large_2^28x4_f16_lf0.95")
+    ap.add_argument("--cpu-workload", default="scale_2^22x4_f16_lf0.95")
+    ap.add_argument("--ref-workload", default="ref_2^20x4_f16_lf0.95")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-warmup", type=int, default=1)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args(argv)
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1")
+    out = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     build,
     fpr_bound,
     fpr_expected,
+    hash_params,
     lib,
     xxh64_u64,
 )

@@ -212,6 +212,26 @@ void cfo_hash_batch(const cfo_filter* F, const uint64_t* keys, uint64_t n,
   for (uint64_t i = 0; i < n; ++i) cfo_hash(F, keys[i], &fp[i], &i1[i], &i2[i]);
 }
 
+int cfo_hash_params_batch(uint64_t m, uint32_t f, uint32_t policy,
+                          const uint64_t* keys, uint64_t n, uint32_t* fp,
+                          uint64_t* i1, uint64_t* i2) {
+  /* Same hash as a filter with these parameters, without allocating one. */
+  cfo_filter F;
+  memset(&F, 0, sizeof F);
+  if (!(f == 8 || f == 16 || f == 32)) return -1;
+  if (policy == CFO_POLICY_XOR ? (!is_pow2(m) || m > (1ULL << 32))
+                               : (m < 2 || m > (1ULL << 32)))
+    return -1;
+  F.m = m;
+  F.f = f;
+  F.policy = policy;
+  F.lane_mask = (f == 32) ? 0xFFFFFFFFu : ((1u << f) - 1u);
+  F.choice = policy == CFO_POLICY_OFFSET ? 1u << (f - 1) : 0u;
+  F.fp_mask = policy == CFO_POLICY_OFFSET ? F.choice - 1u : F.lane_mask;
+  cfo_hash_batch(&F, keys, n, fp, i1, i2);
+  return 0;
+}
+
 /* Alternate location of a tag stored in bucket j.  XOR policy: Eq. 3 is an
  * involution, the tag is unchanged.  Offset policy: the choice bit says
  * whether j is the primary (bit 0: go forward by offset) or the alternate

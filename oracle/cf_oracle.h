@@ -66,7 +66,8 @@ uint64_t cfo_xxh64_u64(uint64_t key, uint64_t seed);
 void cfo_hash(const cfo_filter* F, uint64_t key, uint32_t* fp, uint64_t* i1,
               uint64_t* i2);
 /* The alternate bucket of a tag stored in bucket j (XOR policy: the
- * involution j ^ H(fp); Offset policy: see cfo_alt_offset). */
+ * involution j ^ H(fp); Offset policy: move by offset(fp) in the direction
+ * given by the choice bit). */
 uint64_t cfo_alt(const cfo_filter* F, uint64_t j, uint32_t tag);
 
 /* One operation on one key.  insert returns 1 on success, 0 on failure and
@@ -85,6 +86,10 @@ void cfo_remove_batch(cfo_filter* F, const uint64_t* keys, uint64_t n,
                       uint8_t* flags);
 void cfo_hash_batch(const cfo_filter* F, const uint64_t* keys, uint64_t n,
                     uint32_t* fp, uint64_t* i1, uint64_t* i2);
+/* The same hash for given (m, f, policy) without a table; -1 if invalid. */
+int cfo_hash_params_batch(uint64_t m, uint32_t f, uint32_t policy,
+                          const uint64_t* keys, uint64_t n, uint32_t* fp,
+                          uint64_t* i1, uint64_t* i2);
 
 /* Raw slot access for tests: slot s of bucket j. */
 uint32_t cfo_get_slot(const cfo_filter* F, uint64_t j, uint32_t s);

@@ -74,6 +74,8 @@ def lib():
             for name in ("cfo_contains_batch", "cfo_remove_batch"):
                 getattr(L, name).argtypes = [vp, vp, u64, vp]
             L.cfo_hash_batch.argtypes = [vp, vp, u64, vp, vp, vp]
+            L.cfo_hash_params_batch.restype = ctypes.c_int
+            L.cfo_hash_params_batch.argtypes = [u64, u32, u32, vp, u64, vp, vp, vp]
             L.cfo_get_slot.restype = u32
             L.cfo_get_slot.argtypes = [vp, u64, u32]
             L.cfo_set_slot.argtypes = [vp, u64, u32, u32]
@@ -102,6 +104,20 @@ def _u64(a) -> np.ndarray:
 
 def xxh64_u64(key: int, seed: int = 0) -> int:
     return int(lib().cfo_xxh64_u64(int(key) & (2**64 - 1), seed))
+
+
+def hash_params(keys, m: int, f: int, policy: int = CFO_POLICY_XOR):
+    """(fp, i1, i2) of every key for a filter with m buckets, f-bit
+    fingerprints and the given policy (no table is allocated)."""
+    k = _u64(keys)
+    fp = np.empty(k.size, np.uint32)
+    i1 = np.empty(k.size, np.uint64)
+    i2 = np.empty(k.size, np.uint64)
+    rc = lib().cfo_hash_params_batch(int(m), int(f), int(policy), _ptr(k), k.size,
+                                     _ptr(fp), _ptr(i1), _ptr(i2))
+    if rc != 0:
+        raise ValueError(f"invalid hash parameters m={m} f={f} policy={policy}")
+    return fp, i1, i2
 
 
 def fpr_expected(f: int, b: int, alpha: float, policy: int = CFO_POLICY_XOR) -> float:

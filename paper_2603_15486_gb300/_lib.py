@@ -1,0 +1,97 @@
+"""ctypes loader for libcf.so (the CUDA kernels + C ABI of include/cf.h).
+
+There is no fallback: if the shared library is missing or does not load,
+importing the package raises.  Build it with ``python -c "import
+__graft_entry__ as g; g.build()"`` or ``python paper_2603_15486_gb300/build.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcf.so")
+
+
+class CfConfig(ctypes.Structure):
+    _fields_ = [("num_buckets", ctypes.c_uint64), ("fp_bits", ctypes.c_uint32),
+                ("slots_per_bucket", ctypes.c_uint32),
+                ("max_evictions", ctypes.c_uint32), ("policy", ctypes.c_uint32),
+                ("eviction", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32)]
+
+
+class CfStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "occupancy", "insert_ok", "insert_fail", "remove_ok", "remove_fail",
+        "evictions", "victims", "rollbacks", "rollback_lost", "contention")] + [
+        ("error_word", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32)]
+
+
+# Every symbol include/cf.h declares, with (restype, argtypes).
+_vp, _u64, _u32, _int = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+_st = ctypes.c_int
+_pcfg = ctypes.POINTER(CfConfig)
+SIGNATURES = {
+    "cf_table_bytes": (ctypes.c_size_t, [_pcfg]),
+    "cf_required_bytes": (ctypes.c_size_t, [_pcfg]),
+    "cf_snapshot_bytes": (ctypes.c_size_t, [_vp]),
+    "cf_create": (_st, [_u64, _u32, _u32, _u32, ctypes.POINTER(_vp)]),
+    "cf_create_ex": (_st, [_pcfg, ctypes.POINTER(_vp)]),
+    "cf_create_at": (_st, [_vp, ctypes.c_size_t, _pcfg, ctypes.POINTER(_vp)]),
+    "cf_destroy": (_st, [_vp]),
+    "cf_get_config": (_st, [_vp, _pcfg]),
+    "cf_table_ptr": (_vp, [_vp]),
+    "cf_insert": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_insert_ex": (_st, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "cf_contains": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_remove": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_clear": (_st, [_vp, _vp]),
+    "cf_insert_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_contains_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_remove_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_set_staging_chunk": (_st, [_vp, _u64]),
+    "cf_stats": (_st, [_vp, ctypes.POINTER(CfStats), _vp]),
+    "cf_victims": (_st, [_vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
+    "cf_snapshot": (_st, [_vp, _vp, ctypes.c_size_t, _int, _vp]),
+    "cf_load": (_st, [_vp, _vp, ctypes.c_size_t, _int, _vp]),
+    "cf_count_occupied": (_st, [_vp, ctypes.POINTER(_u64), _vp]),
+    "cf_hash_debug": (_st, [_vp, _u64, _u32, _u64, _u32, _vp, _vp, _vp, _vp]),
+    "cf_debug_insert_serial": (_st, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "cf_status_str": (ctypes.c_char_p, [_st]),
+    "cf_last_error": (ctypes.c_char_p, []),
+    "cf_version": (_int, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libcf.so once; raise if it is missing (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: the CUDA library has not been built "
+            "(run paper_2603_15486_gb300/build.py). There is no CPU fallback.")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class CfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        L = load()
+        msg = L.cf_status_str(status).decode()
+        detail = (L.cf_last_error() or b"").decode()
+        super().__init__(f"{what}: {msg} ({status}) {detail}".strip())
+        self.status = status
+
+
+def check(status: int, what: str):
+    if status != 0:
+        raise CfError(status, what)

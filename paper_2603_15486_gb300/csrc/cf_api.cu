@@ -1,0 +1,662 @@
+// Host side of libcf: the C ABI declared in include/cf.h.
+//
+// One filter = one device allocation laid out as
+//   [control block 256 B][victim log, 16 B per entry][table]
+// (each piece 256-byte aligned), plus library-owned scratch: the eviction
+// work queue of the insert (4 bytes per key of the largest chunk seen) and,
+// for the *_host calls, two staging slots of keys and flags.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "cf.h"
+#include "cf_kernels.cuh"
+
+using cfk::Ctrl;
+using cfk::DevFilter;
+using cfk::Victim;
+
+namespace {
+
+constexpr uint64_t kInsertChunk = 1ull << 28;  // keys per insert launch pair
+constexpr uint32_t kDefaultVictims = 4096;
+constexpr uint32_t kMaxVictims = 1u << 26;
+constexpr uint64_t kDefaultStage = 1ull << 24;
+
+thread_local char g_err[256] = "";
+
+void set_err(const char* what, cudaError_t e) {
+  snprintf(g_err, sizeof g_err, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CF_CUDA(call)                   \
+  do {                                  \
+    cudaError_t e_ = (call);            \
+    if (e_ != cudaSuccess) {            \
+      set_err(#call, e_);               \
+      return CF_ECUDA;                  \
+    }                                   \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+bool valid_config(const cf_config* c) {
+  if (!c) return false;
+  if (!(c->fp_bits == 8 || c->fp_bits == 16 || c->fp_bits == 32)) return false;
+  if (!(c->slots_per_bucket == 4 || c->slots_per_bucket == 8 ||
+        c->slots_per_bucket == 16))
+    return false;
+  if (c->policy == CF_POLICY_XOR) {
+    if (!is_pow2(c->num_buckets) || c->num_buckets > (1ull << 32)) return false;
+  } else if (c->policy == CF_POLICY_OFFSET) {
+    if (c->num_buckets < 2 || c->num_buckets >= (1ull << 32)) return false;
+  } else {
+    return false;
+  }
+  if (c->eviction != CF_EVICT_BFS && c->eviction != CF_EVICT_DFS) return false;
+  if (c->victim_capacity > kMaxVictims) return false;
+  return true;
+}
+
+uint32_t victim_cap(const cf_config* c) {
+  return c->victim_capacity ? c->victim_capacity : kDefaultVictims;
+}
+
+size_t table_bytes(const cf_config* c) {
+  return size_t(c->num_buckets) * c->slots_per_bucket * c->fp_bits / 8;
+}
+
+uint64_t fastmod_magic(uint64_t d) {
+  // floor((2^64 - 1) / d) + 1; d == 1 gives 0, which yields x mod 1 == 0.
+  return d ? (~0ull / d + 1) : 0;
+}
+
+DevFilter make_dev(const cf_config* c, char* mem) {
+  DevFilter d{};
+  d.ctrl = reinterpret_cast<Ctrl*>(mem);
+  d.victims = reinterpret_cast<Victim*>(mem + 256);
+  d.victim_cap = victim_cap(c);
+  d.table = mem + 256 + align256(size_t(d.victim_cap) * sizeof(Victim));
+  d.m = c->num_buckets;
+  d.mask = c->num_buckets - 1;
+  d.fm_m = fastmod_magic(c->num_buckets);
+  d.fm_m1 = fastmod_magic(c->num_buckets - 1);
+  d.max_ev = c->max_evictions;
+  d.eviction = c->eviction;
+  return d;
+}
+
+struct Stage {
+  uint64_t* keys = nullptr;
+  uint8_t* flags = nullptr;
+  cudaEvent_t in_done = nullptr, comp_done = nullptr, out_done = nullptr;
+};
+
+std::mutex g_mu;
+std::unordered_map<int, int> g_sms;
+std::unordered_map<const void*, int> g_occ[64];
+
+}  // namespace
+
+struct cf_filter {
+  cf_config cfg{};
+  int device = 0;
+  char* mem = nullptr;
+  size_t mem_bytes = 0;
+  bool owns = false;
+  DevFilter d{};
+  const cfk::Ops* ops = nullptr;
+  cudaEvent_t last_ev = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool has_last = false;
+  uint32_t* queue = nullptr;
+  uint64_t queue_cap = 0;
+  uint64_t stage_chunk = kDefaultStage;
+  Stage stage[2];
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  bool stage_ready = false;
+};
+
+namespace cfk {
+
+int device_sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_sms.find(dev);
+  if (it != g_sms.end()) return it->second;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  g_sms[dev] = sms;
+  return sms;
+}
+
+int cached_occupancy(const void* fn, int block) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto& m = g_occ[dev & 63];
+  auto it = m.find(fn);
+  if (it != m.end()) return it->second;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0) !=
+          cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  m[fn] = occ;
+  return occ;
+}
+
+}  // namespace cfk
+
+namespace {
+
+cf_status order_on(cf_filter* f, cudaStream_t s) {
+  if (f->has_last && f->last_stream != s)
+    CF_CUDA(cudaStreamWaitEvent(s, f->last_ev, 0));
+  return CF_OK;
+}
+
+cf_status mark(cf_filter* f, cudaStream_t s) {
+  CF_CUDA(cudaEventRecord(f->last_ev, s));
+  f->last_stream = s;
+  f->has_last = true;
+  return CF_OK;
+}
+
+cf_status ensure_queue(cf_filter* f, uint64_t keys) {
+  const uint64_t want = keys < kInsertChunk ? keys : kInsertChunk;
+  if (want <= f->queue_cap) return CF_OK;
+  if (f->queue) CF_CUDA(cudaFree(f->queue));
+  f->queue = nullptr;
+  f->queue_cap = 0;
+  if (cudaMalloc(&f->queue, want * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_err, sizeof g_err, "eviction queue of %llu keys",
+             (unsigned long long)want);
+    return CF_ENOMEM;
+  }
+  f->queue_cap = want;
+  return CF_OK;
+}
+
+cf_status init_filter(cf_filter* f, const cf_config* cfg, char* mem,
+                      size_t bytes, bool owns) {
+  f->cfg = *cfg;
+  if (!f->cfg.victim_capacity) f->cfg.victim_capacity = kDefaultVictims;
+  CF_CUDA(cudaGetDevice(&f->device));
+  f->mem = mem;
+  f->mem_bytes = bytes;
+  f->owns = owns;
+  f->d = make_dev(&f->cfg, mem);
+  f->ops = cfk::get_ops(int(cfg->fp_bits), int(cfg->slots_per_bucket),
+                        int(cfg->policy));
+  if (!f->ops) return CF_ENOTSUP;
+  CF_CUDA(cudaEventCreateWithFlags(&f->last_ev, cudaEventDisableTiming));
+  CF_CUDA(cudaMemset(mem, 0, bytes));
+  CF_CUDA(cudaDeviceSynchronize());
+  return CF_OK;
+}
+
+void free_staging(cf_filter* f) {
+  for (auto& st : f->stage) {
+    if (st.keys) cudaFree(st.keys);
+    if (st.flags) cudaFree(st.flags);
+    if (st.in_done) cudaEventDestroy(st.in_done);
+    if (st.comp_done) cudaEventDestroy(st.comp_done);
+    if (st.out_done) cudaEventDestroy(st.out_done);
+    st = Stage{};
+  }
+  if (f->s_in) cudaStreamDestroy(f->s_in);
+  if (f->s_out) cudaStreamDestroy(f->s_out);
+  f->s_in = f->s_out = nullptr;
+  f->stage_ready = false;
+}
+
+cf_status ensure_staging(cf_filter* f) {
+  if (f->stage_ready) return CF_OK;
+  const uint64_t c = f->stage_chunk;
+  for (auto& st : f->stage) {
+    if (cudaMalloc(&st.keys, c * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&st.flags, c) != cudaSuccess) {
+      cudaGetLastError();
+      free_staging(f);
+      return CF_ENOMEM;
+    }
+    CF_CUDA(cudaEventCreateWithFlags(&st.in_done, cudaEventDisableTiming));
+    CF_CUDA(cudaEventCreateWithFlags(&st.comp_done, cudaEventDisableTiming));
+    CF_CUDA(cudaEventCreateWithFlags(&st.out_done, cudaEventDisableTiming));
+  }
+  CF_CUDA(cudaStreamCreateWithFlags(&f->s_in, cudaStreamNonBlocking));
+  CF_CUDA(cudaStreamCreateWithFlags(&f->s_out, cudaStreamNonBlocking));
+  f->stage_ready = true;
+  return CF_OK;
+}
+
+enum Op { OP_INSERT, OP_CONTAINS, OP_REMOVE };
+
+cf_status run_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
+                 uint8_t* flags, uint32_t* evout, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (op == OP_CONTAINS) {
+    e = f->ops->contains(f->d, keys, n, flags, s);
+  } else if (op == OP_REMOVE) {
+    e = f->ops->remove(f->d, keys, n, flags, s);
+  } else {
+    cf_status st = ensure_queue(f, n);
+    if (st != CF_OK) return st;
+    for (uint64_t off = 0; off < n && e == cudaSuccess; off += kInsertChunk) {
+      const uint64_t len = (n - off) < kInsertChunk ? (n - off) : kInsertChunk;
+      e = f->ops->insert_chunk(f->d, keys + off, uint32_t(len),
+                               flags ? flags + off : nullptr,
+                               evout ? evout + off : nullptr, f->queue, s);
+    }
+  }
+  if (e != cudaSuccess) {
+    set_err("kernel launch", e);
+    return CF_ECUDA;
+  }
+  return CF_OK;
+}
+
+cf_status device_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
+                    uint8_t* flags, uint32_t* evout, void* stream) {
+  if (!f) return CF_EINVAL;
+  if (n == 0) return CF_OK;
+  if (!keys) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  st = run_op(f, op, keys, n, flags, evout, s);
+  if (st != CF_OK) return st;
+  return mark(f, s);
+}
+
+// Host-buffer form: two staging slots; H2D of chunk c+1 (stream s_in)
+// overlaps the kernels of chunk c (the caller's stream) and the D2H of
+// chunk c-1's flags (stream s_out).
+cf_status host_op(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
+                  uint8_t* flags_h, void* stream) {
+  if (!f) return CF_EINVAL;
+  if (n == 0) return CF_OK;
+  if (!keys_h) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = ensure_staging(f);
+  if (st != CF_OK) return st;
+  if (op == OP_INSERT) {
+    st = ensure_queue(f, f->stage_chunk);
+    if (st != CF_OK) return st;
+  }
+  st = order_on(f, s);
+  if (st != CF_OK) return st;
+  const uint64_t chunk = f->stage_chunk;
+  const uint64_t nchunks = (n + chunk - 1) / chunk;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    Stage& sg = f->stage[c & 1];
+    const uint64_t off = c * chunk;
+    const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
+    if (c >= 2) CF_CUDA(cudaStreamWaitEvent(f->s_in, sg.out_done, 0));
+    CF_CUDA(cudaMemcpyAsync(sg.keys, keys_h + off, len * sizeof(uint64_t),
+                            cudaMemcpyHostToDevice, f->s_in));
+    CF_CUDA(cudaEventRecord(sg.in_done, f->s_in));
+    CF_CUDA(cudaStreamWaitEvent(s, sg.in_done, 0));
+    st = run_op(f, op, sg.keys, len, sg.flags, nullptr, s);
+    if (st != CF_OK) return st;
+    CF_CUDA(cudaEventRecord(sg.comp_done, s));
+    CF_CUDA(cudaStreamWaitEvent(f->s_out, sg.comp_done, 0));
+    if (flags_h)
+      CF_CUDA(cudaMemcpyAsync(flags_h + off, sg.flags, len,
+                              cudaMemcpyDeviceToHost, f->s_out));
+    CF_CUDA(cudaEventRecord(sg.out_done, f->s_out));
+  }
+  st = mark(f, s);
+  if (st != CF_OK) return st;
+  CF_CUDA(cudaStreamSynchronize(f->s_out));
+  return CF_OK;
+}
+
+void put32(uint8_t* p, uint32_t v) { memcpy(p, &v, 4); }
+void put64(uint8_t* p, uint64_t v) { memcpy(p, &v, 8); }
+uint32_t get32(const uint8_t* p) { uint32_t v; memcpy(&v, p, 4); return v; }
+uint64_t get64(const uint8_t* p) { uint64_t v; memcpy(&v, p, 8); return v; }
+
+constexpr uint32_t kSnapMagic = 0x31474643u;  // "CFG1"
+constexpr size_t kSnapHdr = 64;
+
+}  // namespace
+
+extern "C" {
+
+const char* cf_last_error(void) { return g_err; }
+
+int cf_version(void) { return 10000; }
+
+const char* cf_status_str(cf_status s) {
+  switch (s) {
+    case CF_OK: return "ok";
+    case CF_EINVAL: return "invalid argument";
+    case CF_ENOMEM: return "out of memory";
+    case CF_ECUDA: return "CUDA error";
+    case CF_ETIMEOUT: return "timeout";
+    case CF_ECONTENTION: return "contention";
+    case CF_EBUSY: return "busy";
+    case CF_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+size_t cf_table_bytes(const cf_config* cfg) {
+  return valid_config(cfg) ? table_bytes(cfg) : 0;
+}
+
+size_t cf_required_bytes(const cf_config* cfg) {
+  if (!valid_config(cfg)) return 0;
+  return 256 + align256(size_t(victim_cap(cfg)) * sizeof(Victim)) +
+         align256(table_bytes(cfg));
+}
+
+size_t cf_snapshot_bytes(const cf_filter* f) {
+  return f ? kSnapHdr + table_bytes(&f->cfg) : 0;
+}
+
+cf_status cf_create_ex(const cf_config* cfg, cf_filter** out) {
+  if (!out || !valid_config(cfg)) return CF_EINVAL;
+  *out = nullptr;
+  const size_t bytes = cf_required_bytes(cfg);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_err, sizeof g_err, "cudaMalloc of %zu bytes failed", bytes);
+    return CF_ENOMEM;
+  }
+  cf_filter* f = new cf_filter();
+  cf_status st = init_filter(f, cfg, mem, bytes, true);
+  if (st != CF_OK) {
+    cf_destroy(f);
+    return st;
+  }
+  *out = f;
+  return CF_OK;
+}
+
+cf_status cf_create(uint64_t num_buckets, uint32_t fp_bits,
+                    uint32_t slots_per_bucket, uint32_t max_evictions,
+                    cf_filter** out) {
+  cf_config c{};
+  c.num_buckets = num_buckets;
+  c.fp_bits = fp_bits;
+  c.slots_per_bucket = slots_per_bucket;
+  c.max_evictions = max_evictions;
+  c.policy = CF_POLICY_XOR;
+  c.eviction = CF_EVICT_BFS;
+  return cf_create_ex(&c, out);
+}
+
+cf_status cf_create_at(void* dev_mem, size_t bytes, const cf_config* cfg,
+                       cf_filter** out) {
+  if (!out || !dev_mem || !valid_config(cfg)) return CF_EINVAL;
+  *out = nullptr;
+  if (bytes < cf_required_bytes(cfg)) return CF_EINVAL;
+  if (reinterpret_cast<uintptr_t>(dev_mem) & 255) return CF_EINVAL;
+  cf_filter* f = new cf_filter();
+  cf_status st = init_filter(f, cfg, static_cast<char*>(dev_mem),
+                             cf_required_bytes(cfg), false);
+  if (st != CF_OK) {
+    cf_destroy(f);
+    return st;
+  }
+  *out = f;
+  return CF_OK;
+}
+
+cf_status cf_destroy(cf_filter* f) {
+  if (!f) return CF_OK;
+  if (f->has_last) cudaEventSynchronize(f->last_ev);
+  free_staging(f);
+  if (f->queue) cudaFree(f->queue);
+  if (f->last_ev) cudaEventDestroy(f->last_ev);
+  if (f->owns && f->mem) cudaFree(f->mem);
+  delete f;
+  return CF_OK;
+}
+
+cf_status cf_get_config(const cf_filter* f, cf_config* out) {
+  if (!f || !out) return CF_EINVAL;
+  *out = f->cfg;
+  return CF_OK;
+}
+
+void* cf_table_ptr(const cf_filter* f) { return f ? f->d.table : nullptr; }
+
+cf_status cf_insert(cf_filter* f, const uint64_t* keys, uint64_t n,
+                    uint8_t* out_flags, void* stream) {
+  return device_op(f, OP_INSERT, keys, n, out_flags, nullptr, stream);
+}
+
+cf_status cf_insert_ex(cf_filter* f, const uint64_t* keys, uint64_t n,
+                       uint8_t* out_flags, uint32_t* evictions_out,
+                       void* stream) {
+  return device_op(f, OP_INSERT, keys, n, out_flags, evictions_out, stream);
+}
+
+cf_status cf_contains(cf_filter* f, const uint64_t* keys, uint64_t n,
+                      uint8_t* out_flags, void* stream) {
+  if (f && n && !out_flags) return CF_EINVAL;  // a query without output
+  return device_op(f, OP_CONTAINS, keys, n, out_flags, nullptr, stream);
+}
+
+cf_status cf_remove(cf_filter* f, const uint64_t* keys, uint64_t n,
+                    uint8_t* out_flags, void* stream) {
+  return device_op(f, OP_REMOVE, keys, n, out_flags, nullptr, stream);
+}
+
+cf_status cf_insert_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                         uint8_t* out_flags_host, void* stream) {
+  return host_op(f, OP_INSERT, keys_host, n, out_flags_host, stream);
+}
+
+cf_status cf_contains_host(cf_filter* f, const uint64_t* keys_host,
+                           uint64_t n, uint8_t* out_flags_host, void* stream) {
+  if (f && n && !out_flags_host) return CF_EINVAL;
+  return host_op(f, OP_CONTAINS, keys_host, n, out_flags_host, stream);
+}
+
+cf_status cf_remove_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                         uint8_t* out_flags_host, void* stream) {
+  return host_op(f, OP_REMOVE, keys_host, n, out_flags_host, stream);
+}
+
+cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk) {
+  if (!f || keys_per_chunk == 0 || keys_per_chunk > kInsertChunk)
+    return CF_EINVAL;
+  if (f->has_last) cudaEventSynchronize(f->last_ev);
+  free_staging(f);
+  f->stage_chunk = keys_per_chunk;
+  return CF_OK;
+}
+
+cf_status cf_clear(cf_filter* f, void* stream) {
+  if (!f) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  CF_CUDA(cudaMemsetAsync(f->d.table, 0, table_bytes(&f->cfg), s));
+  CF_CUDA(cudaMemsetAsync(f->d.ctrl, 0, sizeof(Ctrl), s));
+  return mark(f, s);
+}
+
+cf_status cf_stats(cf_filter* f, cf_stats_t* out, void* stream) {
+  if (!f || !out) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  Ctrl c;
+  CF_CUDA(cudaMemcpyAsync(&c, f->d.ctrl, sizeof c, cudaMemcpyDeviceToHost, s));
+  CF_CUDA(cudaStreamSynchronize(s));
+  out->occupancy = c.occupancy;
+  out->insert_ok = c.insert_ok;
+  out->insert_fail = c.insert_fail;
+  out->remove_ok = c.remove_ok;
+  out->remove_fail = c.remove_fail;
+  out->evictions = c.evictions;
+  out->victims = c.victims;
+  out->rollbacks = c.rollbacks;
+  out->rollback_lost = c.rollback_lost;
+  out->contention = c.contention;
+  out->error_word = c.error_word;
+  out->victim_capacity = f->d.victim_cap;
+  return mark(f, s);
+}
+
+cf_status cf_victims(cf_filter* f, uint32_t* tags_host, uint64_t* buckets_host,
+                     uint64_t max, uint64_t* count, void* stream) {
+  if (!f) return CF_EINVAL;
+  cf_stats_t stt;
+  cf_status st = cf_stats(f, &stt, stream);
+  if (st != CF_OK) return st;
+  uint64_t logged = stt.victims < f->d.victim_cap ? stt.victims : f->d.victim_cap;
+  if (count) *count = logged;
+  uint64_t n = logged < max ? logged : max;
+  if (n == 0) return CF_OK;
+  Victim* tmp = static_cast<Victim*>(malloc(n * sizeof(Victim)));
+  if (!tmp) return CF_ENOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(tmp, f->d.victims, n * sizeof(Victim),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free(tmp);
+    set_err("victims copy", e);
+    return CF_ECUDA;
+  }
+  for (uint64_t i = 0; i < n; ++i) {
+    if (tags_host) tags_host[i] = tmp[i].tag;
+    if (buckets_host) buckets_host[i] = tmp[i].bucket;
+  }
+  free(tmp);
+  return CF_OK;
+}
+
+cf_status cf_snapshot(cf_filter* f, void* dst, size_t bytes, int dst_is_device,
+                      void* stream) {
+  if (!f || !dst || bytes < cf_snapshot_bytes(f)) return CF_EINVAL;
+  cf_stats_t stt;
+  cf_status st = cf_stats(f, &stt, stream);
+  if (st != CF_OK) return st;
+  uint8_t hdr[kSnapHdr] = {0};
+  put32(hdr + 0, kSnapMagic);
+  put32(hdr + 4, 1);
+  put64(hdr + 8, f->cfg.num_buckets);
+  put32(hdr + 16, f->cfg.fp_bits);
+  put32(hdr + 20, f->cfg.slots_per_bucket);
+  put32(hdr + 24, f->cfg.max_evictions);
+  put32(hdr + 28, f->cfg.policy);
+  put64(hdr + 32, stt.occupancy);
+  put64(hdr + 40, table_bytes(&f->cfg));
+  put32(hdr + 48, 1);
+  put32(hdr + 52, f->cfg.eviction);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* d8 = static_cast<uint8_t*>(dst);
+  const cudaMemcpyKind k1 = dst_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  const cudaMemcpyKind k2 = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CF_CUDA(cudaMemcpyAsync(d8, hdr, kSnapHdr, k1, s));
+  CF_CUDA(cudaMemcpyAsync(d8 + kSnapHdr, f->d.table, table_bytes(&f->cfg), k2, s));
+  CF_CUDA(cudaStreamSynchronize(s));
+  return mark(f, s);
+}
+
+cf_status cf_load(cf_filter* f, const void* src, size_t bytes,
+                  int src_is_device, void* stream) {
+  if (!f || !src || bytes < cf_snapshot_bytes(f)) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  uint8_t hdr[kSnapHdr];
+  CF_CUDA(cudaMemcpyAsync(hdr, src, kSnapHdr,
+                          src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+  CF_CUDA(cudaStreamSynchronize(s));
+  if (get32(hdr) != kSnapMagic || get32(hdr + 4) != 1 ||
+      get64(hdr + 8) != f->cfg.num_buckets || get32(hdr + 16) != f->cfg.fp_bits ||
+      get32(hdr + 20) != f->cfg.slots_per_bucket || get32(hdr + 28) != f->cfg.policy ||
+      get64(hdr + 40) != table_bytes(&f->cfg)) {
+    snprintf(g_err, sizeof g_err, "snapshot header does not match the filter");
+    return CF_EINVAL;
+  }
+  const uint8_t* s8 = static_cast<const uint8_t*>(src);
+  CF_CUDA(cudaMemcpyAsync(f->d.table, s8 + kSnapHdr, table_bytes(&f->cfg),
+                          src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CF_CUDA(cudaMemsetAsync(f->d.ctrl, 0, sizeof(Ctrl), s));
+  cudaError_t e = f->ops->count(f->d, &f->d.ctrl->occupancy, s);
+  if (e != cudaSuccess) {
+    set_err("count kernel", e);
+    return CF_ECUDA;
+  }
+  CF_CUDA(cudaStreamSynchronize(s));
+  return mark(f, s);
+}
+
+cf_status cf_count_occupied(cf_filter* f, uint64_t* out, void* stream) {
+  if (!f || !out) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  CF_CUDA(cudaMemsetAsync(&f->d.ctrl->scratch_count, 0, 8, s));
+  cudaError_t e = f->ops->count(f->d, &f->d.ctrl->scratch_count, s);
+  if (e != cudaSuccess) {
+    set_err("count kernel", e);
+    return CF_ECUDA;
+  }
+  unsigned long long v = 0;
+  CF_CUDA(cudaMemcpyAsync(&v, &f->d.ctrl->scratch_count, 8, cudaMemcpyDeviceToHost, s));
+  CF_CUDA(cudaStreamSynchronize(s));
+  *out = v;
+  return mark(f, s);
+}
+
+cf_status cf_hash_debug(const uint64_t* keys, uint64_t n, uint32_t fp_bits,
+                        uint64_t num_buckets, uint32_t policy, uint32_t* fp,
+                        uint64_t* i1, uint64_t* i2, void* stream) {
+  cf_config c{};
+  c.num_buckets = num_buckets;
+  c.fp_bits = fp_bits;
+  c.slots_per_bucket = 4;
+  c.policy = policy;
+  if (!valid_config(&c)) return CF_EINVAL;
+  if (n == 0) return CF_OK;
+  if (!keys) return CF_EINVAL;
+  DevFilter d = make_dev(&c, nullptr);
+  const cfk::Ops* ops = cfk::get_ops(int(fp_bits), 4, int(policy));
+  if (!ops) return CF_ENOTSUP;
+  cudaError_t e = ops->hash(d, keys, n, fp, i1, i2, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    set_err("hash kernel", e);
+    return CF_ECUDA;
+  }
+  return CF_OK;
+}
+
+cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
+                                 uint64_t n, uint8_t* out_flags,
+                                 uint32_t* evictions_out, void* stream) {
+  if (!f) return CF_EINVAL;
+  if (n == 0) return CF_OK;
+  if (!keys) return CF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  cudaError_t e = f->ops->insert_serial(f->d, keys, n, out_flags, evictions_out, s);
+  if (e != cudaSuccess) {
+    set_err("serial insert", e);
+    return CF_ECUDA;
+  }
+  return mark(f, s);
+}
+
+}  // extern "C"

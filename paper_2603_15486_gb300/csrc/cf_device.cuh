@@ -1,0 +1,589 @@
+// Device primitives and per-key algorithms of the cuckoo filter (sm_103a).
+//
+// Paper: "Cuckoo-GPU: Accelerating Cuckoo Filters on Modern GPUs" (Dortmann,
+// Vieth, Schmidt, 2026).  Hashing: Sec. 2.1 Eq. 1-3 and Sec. 4.3 step 1.
+// Layout: Sec. 4.2 / Fig. 2.  TryInsert: Alg. 1.  Find: Alg. 2.  TryRemove:
+// Alg. 3.  BFS eviction: Sec. 4.6.1.  DFS chain: Alg. 1 phase 2.  Offset
+// policy: Sec. 4.6.2.
+//
+// Every loop that waits on another thread's progress (CAS retry loops) has a
+// fixed iteration bound; running out of it is reported as contention in the
+// key's flag and in the control block, never by trapping.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "cf_types.h"
+
+namespace cfk {
+
+// Bound of every CAS retry loop on one word.
+constexpr int kMaxCas = 1 << 12;
+
+// ---------------------------------------------------------------------------
+// Geometry: F-bit tags, B slots per bucket, bucket policy.
+// ---------------------------------------------------------------------------
+template <int F_, int B_, int POLICY_>
+struct Geo {
+  static constexpr int F = F_;
+  static constexpr int B = B_;
+  static constexpr int POLICY = POLICY_;
+  static constexpr bool kW32 = (F * B == 32);
+  using Word = std::conditional_t<kW32, unsigned int, unsigned long long>;
+  static constexpr int kWordBits = kW32 ? 32 : 64;
+  static constexpr int kTpw = kWordBits / F;          // tags per word
+  static constexpr int kWpb = (F * B) / kWordBits;    // words per bucket
+  static constexpr int kBucketBytes = F * B / 8;
+  static constexpr Word kLaneMask =
+      F == 32 ? Word(0xFFFFFFFFu) : Word((Word(1) << F) - 1);
+  static constexpr Word ones() {
+    Word w = 0;
+    for (int l = 0; l < kTpw; ++l) w |= Word(1) << (l * F);
+    return w;
+  }
+  static constexpr Word kOnes = ones();                 // 1 in every lane
+  static constexpr Word kLow = kOnes * (kLaneMask >> 1);  // 0x7F.. per lane
+  static constexpr uint32_t kChoice = POLICY == 1 ? (1u << (F - 1)) : 0u;
+  static constexpr uint32_t kFpMask =
+      POLICY == 1 ? kChoice - 1u : uint32_t(kLaneMask);
+  static_assert(kWpb >= 1 && (kWpb & (kWpb - 1)) == 0, "words per bucket");
+};
+
+template <class G>
+struct Bucket {
+  typename G::Word w[G::kWpb];
+};
+
+// ---------------------------------------------------------------------------
+// Loads.  Queries use non-coherent, L1-bypassing loads (the table is
+// read-only while a query runs).  Mutating kernels use .cg loads (L2, which
+// is coherent with the atomics) so that a thread never reads a stale L1 copy
+// of a word it or another thread has just changed by CAS.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int ld_nc_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_nc_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void ld_nc_v2(const unsigned long long* p,
+                                         unsigned long long& a,
+                                         unsigned long long& b) {
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0,%1}, [%2];"
+               : "=l"(a), "=l"(b) : "l"(p));
+}
+__device__ __forceinline__ void ld_nc_v4(const unsigned long long* p,
+                                         unsigned long long& a,
+                                         unsigned long long& b,
+                                         unsigned long long& c,
+                                         unsigned long long& d) {
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+__device__ __forceinline__ unsigned int ld_cg_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void ld_cg_v2(const unsigned long long* p,
+                                         unsigned long long& a,
+                                         unsigned long long& b) {
+  asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+__device__ __forceinline__ void ld_cg_v4(const unsigned long long* p,
+                                         unsigned long long& a,
+                                         unsigned long long& b,
+                                         unsigned long long& c,
+                                         unsigned long long& d) {
+  asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+// Streaming loads of the key array (read once).
+__device__ __forceinline__ unsigned long long ld_stream_u64(const uint64_t* p) {
+  unsigned long long v;
+  asm volatile("ld.global.cs.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+template <class G, bool NC>
+__device__ __forceinline__ Bucket<G> load_bucket(const typename G::Word* p) {
+  Bucket<G> b;
+  if constexpr (G::kW32) {
+    b.w[0] = NC ? ld_nc_u32(p) : ld_cg_u32(p);
+  } else if constexpr (G::kWpb == 1) {
+    b.w[0] = NC ? ld_nc_u64(p) : ld_cg_u64(p);
+  } else if constexpr (G::kWpb == 2) {
+    if (NC) ld_nc_v2(p, b.w[0], b.w[1]); else ld_cg_v2(p, b.w[0], b.w[1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < G::kWpb; q += 4) {
+      if (NC)
+        ld_nc_v4(p + q, b.w[q], b.w[q + 1], b.w[q + 2], b.w[q + 3]);
+      else
+        ld_cg_v4(p + q, b.w[q], b.w[q + 1], b.w[q + 2], b.w[q + 3]);
+    }
+  }
+  return b;
+}
+
+template <class G>
+__device__ __forceinline__ typename G::Word select_word(const Bucket<G>& b,
+                                                        int wi) {
+  typename G::Word w = b.w[0];
+#pragma unroll
+  for (int q = 1; q < G::kWpb; ++q)
+    if (q == wi) w = b.w[q];
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// SWAR on one word (Alg. 1-3 "ZeroMask", "HasZeroSegment", "BroadcastTag").
+// zero_lanes sets the top bit of exactly the lanes that are zero: adding
+// 0x7F..F to the low bits of a lane cannot carry into the next lane, so the
+// mask is exact per lane (needed to pick a lane to CAS, not only to test).
+// ---------------------------------------------------------------------------
+template <class G>
+__device__ __forceinline__ typename G::Word zero_lanes(typename G::Word x) {
+  return ~(((x & G::kLow) + G::kLow) | x | G::kLow);
+}
+template <class G>
+__device__ __forceinline__ typename G::Word broadcast(uint32_t tag) {
+  return typename G::Word(tag) * G::kOnes;
+}
+template <class G>
+__device__ __forceinline__ int first_lane(typename G::Word mask) {
+  int bit;
+  if constexpr (G::kW32)
+    bit = __ffs(mask) - 1;
+  else
+    bit = __ffsll((long long)mask) - 1;
+  return bit / G::F;
+}
+template <class G>
+__device__ __forceinline__ uint32_t get_lane(typename G::Word w, int lane) {
+  return uint32_t((w >> (lane * G::F)) & G::kLaneMask);
+}
+template <class G>
+__device__ __forceinline__ typename G::Word replace_lane(typename G::Word w,
+                                                         int lane,
+                                                         uint32_t tag) {
+  using W = typename G::Word;
+  const int sh = lane * G::F;
+  return (w & ~(G::kLaneMask << sh)) | (W(tag) << sh);
+}
+template <class G>
+__device__ __forceinline__ uint32_t get_slot(const Bucket<G>& b, uint32_t s) {
+  return get_lane<G>(select_word<G>(b, int(s / G::kTpw)), int(s % G::kTpw));
+}
+template <class G>
+__device__ __forceinline__ bool has_empty(const Bucket<G>& b) {
+  typename G::Word acc = 0;
+#pragma unroll
+  for (int q = 0; q < G::kWpb; ++q) acc |= zero_lanes<G>(b.w[q]);
+  return acc != 0;
+}
+template <class G>
+__device__ __forceinline__ bool bucket_has(const Bucket<G>& b, uint32_t tag) {
+  const typename G::Word pat = broadcast<G>(tag);
+  typename G::Word acc = 0;
+#pragma unroll
+  for (int q = 0; q < G::kWpb; ++q) acc |= zero_lanes<G>(b.w[q] ^ pat);
+  return acc != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Hashing (Eq. 1-3, Sec. 4.3): XXH64 of the key's 8 little-endian bytes,
+// seed 0, written from the public XXH64 specification.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kP1 = 0x9E3779B185EBCA87ull;
+constexpr uint64_t kP2 = 0xC2B2AE3D27D4EB4Full;
+constexpr uint64_t kP3 = 0x165667B19E3779F9ull;
+constexpr uint64_t kP4 = 0x85EBCA77C2B2AE63ull;
+constexpr uint64_t kP5 = 0x27D4EB2F165667C5ull;
+
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) {
+  return (x << r) | (x >> (64 - r));
+}
+
+__device__ __forceinline__ uint64_t xxh64_u64(uint64_t key) {
+  uint64_t acc = kP5 + 8u;
+  acc ^= rotl64(key * kP2, 31) * kP1;
+  acc = rotl64(acc, 27) * kP1 + kP4;
+  acc ^= acc >> 33;
+  acc *= kP2;
+  acc ^= acc >> 29;
+  acc *= kP3;
+  acc ^= acc >> 32;
+  return acc;
+}
+
+// H(fp) of Eq. 3: XXH64 of the fingerprint, low 32 bits.
+__device__ __forceinline__ uint32_t fp_hash(uint32_t fp) {
+  return uint32_t(xxh64_u64(uint64_t(fp)));
+}
+
+// x mod d for 32-bit x and 1 <= d < 2^32, with M = floor((2^64-1)/d) + 1
+// precomputed on the host (Lemire, Kaser, Kurz, "Faster remainder by direct
+// computation", 2019).
+__device__ __forceinline__ uint64_t fastmod32(uint32_t x, uint64_t M,
+                                              uint64_t d) {
+  return __umul64hi(M * uint64_t(x), d);
+}
+
+struct KeyHash {
+  uint64_t h;
+  uint64_t i1, i2;
+  uint32_t fp;  // fingerprint proper (without the choice bit)
+};
+
+template <class G>
+__device__ __forceinline__ uint64_t offset_of(const DevFilter& d, uint32_t fp) {
+  return 1u + fastmod32(fp_hash(fp), d.fm_m1, d.m - 1);
+}
+
+template <class G>
+__device__ __forceinline__ KeyHash hash_key(const DevFilter& d, uint64_t key) {
+  KeyHash k;
+  k.h = xxh64_u64(key);
+  uint32_t raw = uint32_t(k.h >> 32) & G::kFpMask;
+  k.fp = raw ? raw : 1u;
+  if constexpr (G::POLICY == 0) {
+    k.i1 = uint64_t(uint32_t(k.h)) & d.mask;
+    k.i2 = k.i1 ^ (uint64_t(fp_hash(k.fp)) & d.mask);
+  } else {
+    k.i1 = fastmod32(uint32_t(k.h), d.fm_m, d.m);
+    uint64_t j = k.i1 + offset_of<G>(d, k.fp);
+    k.i2 = j >= d.m ? j - d.m : j;
+  }
+  return k;
+}
+
+// Alternate bucket of a tag stored in bucket j; *moved is the tag as it is
+// stored there (the Offset policy flips the choice bit).
+template <class G>
+__device__ __forceinline__ uint64_t alt_of(const DevFilter& d, uint64_t j,
+                                           uint32_t tag, uint32_t& moved) {
+  if constexpr (G::POLICY == 0) {
+    moved = tag;
+    return j ^ (uint64_t(fp_hash(tag)) & d.mask);
+  } else {
+    const uint32_t fp = tag & G::kFpMask;
+    const uint64_t off = offset_of<G>(d, fp);
+    if (tag & G::kChoice) {
+      moved = fp;
+      return j >= off ? j - off : j + d.m - off;
+    }
+    moved = fp | G::kChoice;
+    uint64_t a = j + off;
+    return a >= d.m ? a - d.m : a;
+  }
+}
+
+// Per-key random stream for the eviction loop: splitmix64 seeded with the
+// key's 64-bit hash (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t rng_next(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// Single-key bucket operations (used by the eviction loops, the serial
+// kernel and the rollback path).
+// ---------------------------------------------------------------------------
+enum : int { TI_FULL = 0, TI_OK = 1, TI_CONTENTION = -1 };
+
+template <class G>
+__device__ __forceinline__ typename G::Word* bucket_ptr(const DevFilter& d,
+                                                        uint64_t j) {
+  return reinterpret_cast<typename G::Word*>(d.table) + j * G::kWpb;
+}
+
+// TryInsert (Alg. 1): start word (tag mod b) / tpw, wrap-around scan, CAS
+// the tag into the lowest empty lane; on a lost CAS continue from the
+// returned word.
+template <class G>
+__device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag) {
+  using W = typename G::Word;
+  W* base = bucket_ptr<G>(d, j);
+  const Bucket<G> bk = load_bucket<G, false>(base);
+  const int start = int((tag % G::B) / G::kTpw);
+#pragma unroll
+  for (int i = 0; i < G::kWpb; ++i) {
+    const int w = (start + i) & (G::kWpb - 1);
+    W cur = select_word<G>(bk, w);
+    for (int tries = 0;; ++tries) {
+      const W z = zero_lanes<G>(cur);
+      if (!z) break;
+      if (tries == kMaxCas) return TI_CONTENTION;
+      const int lane = first_lane<G>(z);
+      const W desired = cur | (W(tag) << (lane * G::F));
+      const W old = atomicCAS(base + w, cur, desired);
+      if (old == cur) return TI_OK;
+      cur = old;
+    }
+  }
+  return TI_FULL;
+}
+
+// TryRemove (Alg. 3): same scan order; CAS the lowest matching lane to 0.
+template <class G>
+__device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag) {
+  using W = typename G::Word;
+  W* base = bucket_ptr<G>(d, j);
+  const Bucket<G> bk = load_bucket<G, false>(base);
+  const W pat = broadcast<G>(tag);
+  const int start = int((tag % G::B) / G::kTpw);
+#pragma unroll
+  for (int i = 0; i < G::kWpb; ++i) {
+    const int w = (start + i) & (G::kWpb - 1);
+    W cur = select_word<G>(bk, w);
+    for (int tries = 0;; ++tries) {
+      const W z = zero_lanes<G>(cur ^ pat);
+      if (!z) break;
+      if (tries == kMaxCas) return TI_CONTENTION;
+      const int lane = first_lane<G>(z);
+      const W desired = cur & ~(G::kLaneMask << (lane * G::F));
+      const W old = atomicCAS(base + w, cur, desired);
+      if (old == cur) return TI_OK;
+      cur = old;
+    }
+  }
+  return TI_FULL;
+}
+
+struct EvictCounters {
+  uint32_t rollbacks = 0, rollback_lost = 0, contention = 0;
+};
+
+// Result codes of the eviction loops (the key's flag).
+enum : int { EV_FAIL = 0, EV_OK = 1, EV_CONTENTION = 2 };
+
+// BFS eviction heuristic (Sec. 4.6.1).  Starts with `tag` destined for the
+// full bucket `cur`.  Each round inspects b/2 consecutive slots from a random
+// start; if some candidate's alternate bucket has an empty slot, the
+// candidate is moved there and the new tag takes its slot (two steps, the
+// first undone if the second CAS finds the slot changed).  Otherwise the
+// last candidate is swapped out and the search restarts from its alternate
+// bucket.  The b/2 alternate-bucket probes of a round are independent loads
+// and are issued together.
+template <class G>
+__device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
+                         uint32_t tag, uint32_t& ev, uint32_t& vt,
+                         uint64_t& vb, EvictCounters& ec) {
+  using W = typename G::Word;
+  constexpr int H = G::B / 2;
+  while (ev < d.max_ev) {
+    const uint32_t start = uint32_t(rng_next(rng) & (G::B - 1));
+    W* cbase = bucket_ptr<G>(d, cur);
+    Bucket<G> bk = load_bucket<G, false>(cbase);
+    if (has_empty<G>(bk)) {
+      // Only reachable under concurrency (a slot freed by a rollback).
+      const int r = try_insert<G>(d, cur, tag);
+      if (r == TI_OK) return EV_OK;
+      bk = load_bucket<G, false>(cbase);
+    }
+    uint32_t t[H], mv[H];
+    uint64_t a[H];
+    bool open[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      t[k] = get_slot<G>(bk, (start + k) & (G::B - 1));
+      a[k] = alt_of<G>(d, cur, t[k], mv[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      open[k] = false;
+      if (t[k] != 0 && a[k] != cur)
+        open[k] = has_empty<G>(load_bucket<G, false>(bucket_ptr<G>(d, a[k])));
+    }
+#pragma unroll 1
+    for (int k = 0; k < H; ++k) {
+      if (!open[k]) continue;
+      const int r = try_insert<G>(d, a[k], mv[k]);
+      if (r != TI_OK) {
+        if (r == TI_CONTENTION) ec.contention++;
+        continue;
+      }
+      const uint32_t c = (start + k) & (G::B - 1);
+      const int wi = int(c / G::kTpw), lane = int(c % G::kTpw);
+      W w = select_word<G>(bk, wi);
+      bool placed = false;
+      for (int tries = 0; tries < kMaxCas; ++tries) {
+        if (get_lane<G>(w, lane) != t[k]) break;  // the slot changed
+        const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, tag));
+        if (old == w) {
+          placed = true;
+          break;
+        }
+        w = old;
+      }
+      if (placed) {
+        ev++;
+        return EV_OK;
+      }
+      // Undo step 1: remove one copy of the candidate from its alternate
+      // bucket, or from the bucket it may have been moved back to.
+      ec.rollbacks++;
+      if (try_remove<G>(d, a[k], mv[k]) != TI_OK) {
+        uint32_t back;
+        const uint64_t aa = alt_of<G>(d, a[k], mv[k], back);
+        if (try_remove<G>(d, aa, back) != TI_OK) ec.rollback_lost++;
+      }
+      bk = load_bucket<G, false>(cbase);
+    }
+    // No shallow path: swap the last candidate out.
+    const uint32_t c = (start + H - 1) & (G::B - 1);
+    const int wi = int(c / G::kTpw), lane = int(c % G::kTpw);
+    W w = select_word<G>(bk, wi);
+    bool swapped = false;
+    uint32_t evicted = 0;
+    for (int tries = 0; tries < kMaxCas; ++tries) {
+      const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, tag));
+      if (old == w) {
+        evicted = get_lane<G>(w, lane);
+        swapped = true;
+        break;
+      }
+      w = old;
+    }
+    if (!swapped) {
+      ec.contention++;
+      vt = tag;
+      vb = cur;
+      return EV_CONTENTION;
+    }
+    ev++;
+    if (evicted == 0) return EV_OK;
+    uint32_t moved;
+    cur = alt_of<G>(d, cur, evicted, moved);
+    tag = moved;
+    const int r = try_insert<G>(d, cur, tag);
+    if (r == TI_OK) return EV_OK;
+    if (r == TI_CONTENTION) {
+      ec.contention++;
+      vt = tag;
+      vb = cur;
+      return EV_CONTENTION;
+    }
+  }
+  vt = tag;
+  vb = cur;
+  return EV_FAIL;
+}
+
+// Greedy DFS chain (Alg. 1 phase 2): swap the tag into a random slot of cur,
+// carry the evicted tag to its alternate bucket, try a direct insert there.
+template <class G>
+__device__ int evict_dfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
+                         uint32_t tag, uint32_t& ev, uint32_t& vt,
+                         uint64_t& vb, EvictCounters& ec) {
+  using W = typename G::Word;
+  while (ev < d.max_ev) {
+    const uint32_t s = uint32_t(rng_next(rng) & (G::B - 1));
+    const int wi = int(s / G::kTpw), lane = int(s % G::kTpw);
+    W* wp = bucket_ptr<G>(d, cur) + wi;
+    W w;
+    if constexpr (G::kW32) w = ld_cg_u32(wp); else w = ld_cg_u64(wp);
+    bool swapped = false;
+    uint32_t evicted = 0;
+    for (int tries = 0; tries < kMaxCas; ++tries) {
+      const W old = atomicCAS(wp, w, replace_lane<G>(w, lane, tag));
+      if (old == w) {
+        evicted = get_lane<G>(w, lane);
+        swapped = true;
+        break;
+      }
+      w = old;
+    }
+    if (!swapped) {
+      ec.contention++;
+      vt = tag;
+      vb = cur;
+      return EV_CONTENTION;
+    }
+    ev++;
+    if (evicted == 0) return EV_OK;
+    uint32_t moved;
+    cur = alt_of<G>(d, cur, evicted, moved);
+    tag = moved;
+    const int r = try_insert<G>(d, cur, tag);
+    if (r == TI_OK) return EV_OK;
+    if (r == TI_CONTENTION) {
+      ec.contention++;
+      vt = tag;
+      vb = cur;
+      return EV_CONTENTION;
+    }
+  }
+  vt = tag;
+  vb = cur;
+  return EV_FAIL;
+}
+
+// Phase 2 of Alg. 1 for one key whose direct insertion failed: pick i1 or
+// i2 with the key's first random draw, then run the eviction loop.
+template <class G>
+__device__ int evict_key(const DevFilter& d, const KeyHash& kh, uint32_t& ev,
+                         uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
+  const uint32_t t1 = kh.fp, t2 = kh.fp | G::kChoice;
+  ev = 0;
+  if (d.max_ev == 0) {
+    vt = t1;
+    vb = kh.i1;
+    return EV_FAIL;
+  }
+  uint64_t rng = kh.h;
+  const bool first = (rng_next(rng) & 1) == 0;
+  const uint64_t cur = first ? kh.i1 : kh.i2;
+  const uint32_t tag = first ? t1 : t2;
+  return d.eviction == 1 ? evict_dfs<G>(d, rng, cur, tag, ev, vt, vb, ec)
+                         : evict_bfs<G>(d, rng, cur, tag, ev, vt, vb, ec);
+}
+
+__device__ __forceinline__ void log_victim(const DevFilter& d, uint32_t tag,
+                                           uint64_t bucket) {
+  const unsigned long long i = atomicAdd(&d.ctrl->victims, 1ull);
+  if (i < d.victim_cap) {
+    d.victims[i].tag = tag;
+    d.victims[i].bucket = bucket;
+  } else {
+    atomicOr(&d.ctrl->error_word, 2u);
+  }
+}
+
+// Block-wide sum of a per-thread count, added to *dst by one atomic per
+// block (the hierarchical reduction of Sec. 4.3: warp shuffle, shared
+// memory, one global atomic).  Every thread of the block must call it.
+__device__ __forceinline__ void block_add(unsigned long long* dst, uint32_t v,
+                                          bool negate = false) {
+  __shared__ unsigned long long s_part[32];
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s_part[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long y = lane < nw ? s_part[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xFFFFFFFFu, y, o);
+    if (lane == 0 && y) atomicAdd(dst, negate ? (0ull - y) : y);
+  }
+  __syncthreads();
+}
+
+}  // namespace cfk

@@ -1,0 +1,24 @@
+// Kernel instantiations for 8-bit fingerprints (b in {4, 8, 16}, XOR and
+// Offset bucket policies).
+#include "cf_kernels.cuh"
+
+namespace cfk {
+
+const Ops* ops_f8(int b, int policy) {
+  if (policy == 0) {
+    switch (b) {
+      case 4: return ops_for<Geo<8, 4, 0>>();
+      case 8: return ops_for<Geo<8, 8, 0>>();
+      case 16: return ops_for<Geo<8, 16, 0>>();
+    }
+  } else if (policy == 1) {
+    switch (b) {
+      case 4: return ops_for<Geo<8, 4, 1>>();
+      case 8: return ops_for<Geo<8, 8, 1>>();
+      case 16: return ops_for<Geo<8, 16, 1>>();
+    }
+  }
+  return nullptr;
+}
+
+}  // namespace cfk

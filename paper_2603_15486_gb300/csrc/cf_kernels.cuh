@@ -1,0 +1,533 @@
+// Kernels of the cuckoo filter and their launchers, templated on the
+// geometry (fingerprint bits, slots per bucket, bucket policy).
+//
+// Work distribution: a persistent grid (SM count x resident blocks) walks
+// the batch in warp tiles of 32*K keys.  Lane l of a warp owns keys
+// tile + k*32 + l for k < K, so every key load and flag store of a warp is
+// one contiguous 256 B / 32 B access, and each thread keeps K independent
+// random bucket accesses in flight (memory-level parallelism for HBM).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cf_device.cuh"
+
+namespace cfk {
+
+constexpr int kBlock = 256;
+
+// Keys per thread: enough independent bucket loads in flight while keeping
+// K buckets in registers.
+template <class G>
+struct Tiles {
+  static constexpr int K = G::kBucketBytes <= 8 ? 8
+                           : G::kBucketBytes <= 16 ? 4
+                           : G::kBucketBytes <= 32 ? 2 : 1;
+};
+
+__device__ __forceinline__ void st_flag(uint8_t* p, uint8_t v) {
+  asm volatile("st.global.cs.u8 [%0], %1;" ::"l"(p), "h"((unsigned short)v));
+}
+
+// ---------------------------------------------------------------------------
+// K keys' CAS attempts on one bucket each, issued together per round.
+// INSERT: CAS the tag into the lowest empty lane (TryInsert, Alg. 1).
+// REMOVE: CAS the lowest lane equal to the tag to zero (TryRemove, Alg. 3).
+// Scan order per key: words from (tag mod b) / tpw with wrap-around.
+// ---------------------------------------------------------------------------
+template <class G, int K, bool INSERT>
+__device__ __forceinline__ void cas_many(const DevFilter& d,
+                                         const uint64_t (&bkt)[K],
+                                         const uint32_t (&tag)[K],
+                                         const bool (&act)[K], int (&res)[K]) {
+  using W = typename G::Word;
+  Bucket<G> bk[K];
+  W cur[K];
+  int start[K], pos[K];
+  bool live[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    res[k] = TI_FULL;
+    live[k] = act[k];
+    if (live[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    start[k] = int((tag[k] % G::B) / G::kTpw);
+    pos[k] = G::kWpb;
+    cur[k] = 0;
+    if (!live[k]) continue;
+    const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
+#pragma unroll
+    for (int i = G::kWpb - 1; i >= 0; --i) {
+      const W w = select_word<G>(bk[k], (start[k] + i) & (G::kWpb - 1));
+      if (zero_lanes<G>(w ^ pat)) {
+        pos[k] = i;
+        cur[k] = w;
+      }
+    }
+    if (pos[k] == G::kWpb) live[k] = false;
+  }
+  for (int round = 0; round < kMaxCas; ++round) {
+    W old[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!live[k]) continue;
+      const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
+      const int lane = first_lane<G>(zero_lanes<G>(cur[k] ^ pat));
+      const W desired = INSERT ? (cur[k] | (W(tag[k]) << (lane * G::F)))
+                               : (cur[k] & ~(G::kLaneMask << (lane * G::F)));
+      W* p = bucket_ptr<G>(d, bkt[k]) + ((start[k] + pos[k]) & (G::kWpb - 1));
+      old[k] = atomicCAS(p, cur[k], desired);
+    }
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!live[k]) continue;
+      if (old[k] == cur[k]) {
+        res[k] = TI_OK;
+        live[k] = false;
+        continue;
+      }
+      cur[k] = old[k];
+      const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
+      if (!zero_lanes<G>(cur[k] ^ pat)) {
+        // This word has nothing left; continue with the next word of the
+        // scan that (as first loaded) had a candidate lane.
+        int np = G::kWpb;
+#pragma unroll
+        for (int i = G::kWpb - 1; i >= 1; --i) {
+          if (i <= pos[k]) continue;
+          const W w = select_word<G>(bk[k], (start[k] + i) & (G::kWpb - 1));
+          if (zero_lanes<G>(w ^ pat)) {
+            np = i;
+            cur[k] = w;
+          }
+        }
+        pos[k] = np;
+        if (np == G::kWpb) {
+          live[k] = false;
+          continue;
+        }
+      }
+      any = true;
+    }
+    if (!any) break;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (live[k]) res[k] = TI_CONTENTION;
+}
+
+// ---------------------------------------------------------------------------
+// Insert, phase 1 (Alg. 1 direct insertion into i1, then i2).  Keys whose
+// two buckets are both full are appended to the eviction queue (warp
+// ballot + one atomic per warp); phase 2 runs them in k_insert_evict so that
+// the few long eviction chains do not hold whole warps of finished keys.
+// ---------------------------------------------------------------------------
+template <class G, int K>
+__global__ void __launch_bounds__(kBlock)
+k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
+                uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
+                uint32_t* __restrict__ queue) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t n_ok = 0, n_cont = 0;
+  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K)) {
+    uint32_t idx[K];
+    bool valid[K];
+    KeyHash kh[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint64_t i = base + uint64_t(k) * 32 + lane;
+      valid[k] = i < n;
+      idx[k] = uint32_t(i);
+      kh[k] = hash_key<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
+    }
+    uint64_t bkt[K];
+    uint32_t tag[K];
+    int r1[K], r2[K];
+    bool act[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      bkt[k] = kh[k].i1;
+      tag[k] = kh[k].fp;
+      act[k] = valid[k];
+    }
+    cas_many<G, K, true>(d, bkt, tag, act, r1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      bkt[k] = kh[k].i2;
+      tag[k] = kh[k].fp | G::kChoice;
+      act[k] = valid[k] && r1[k] == TI_FULL;
+    }
+    cas_many<G, K, true>(d, bkt, tag, act, r2);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ok = valid[k] && (r1[k] == TI_OK || (r1[k] == TI_FULL && r2[k] == TI_OK));
+      const bool cont = valid[k] && (r1[k] == TI_CONTENTION ||
+                                     (r1[k] == TI_FULL && r2[k] == TI_CONTENTION));
+      const bool need = valid[k] && r1[k] == TI_FULL && r2[k] == TI_FULL;
+      if (ok) {
+        n_ok++;
+        if (flags) st_flag(flags + idx[k], 1);
+        if (evout) evout[idx[k]] = 0;
+      } else if (cont) {
+        n_cont++;
+        log_victim(d, r1[k] == TI_CONTENTION ? kh[k].fp : (kh[k].fp | G::kChoice),
+                   r1[k] == TI_CONTENTION ? kh[k].i1 : kh[k].i2);
+        if (flags) st_flag(flags + idx[k], 2);
+        if (evout) evout[idx[k]] = 0;
+      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
+      if (bal) {
+        const int leader = __ffs(bal) - 1;
+        uint32_t pos = 0;
+        if (int(lane) == leader) pos = atomicAdd(&d.ctrl->queue_count, __popc(bal));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+        if (need) queue[pos + __popc(bal & ((1u << lane) - 1u))] = idx[k];
+      }
+    }
+  }
+  block_add(&d.ctrl->occupancy, n_ok);
+  block_add(&d.ctrl->insert_ok, n_ok);
+  block_add(&d.ctrl->insert_fail, n_cont);
+  block_add(&d.ctrl->contention, n_cont);
+}
+
+// Insert, phase 2: the eviction loop for every queued key.  The queue length
+// is read on the device, so no host round trip separates the two phases.
+// The last block to finish resets the queue for the next batch.
+template <class G>
+__global__ void __launch_bounds__(kBlock)
+k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
+               uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
+               const uint32_t* __restrict__ queue) {
+  const uint32_t qn = *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
+  uint32_t n_ok = 0, n_fail = 0, n_ev = 0;
+  EvictCounters ec;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < qn;
+       e += gridDim.x * blockDim.x) {
+    const uint32_t i = queue[e];
+    const KeyHash kh = hash_key<G>(d, keys[i]);
+    uint32_t ev = 0, vt = 0;
+    uint64_t vb = 0;
+    const int r = evict_key<G>(d, kh, ev, vt, vb, ec);
+    if (r != EV_OK) log_victim(d, vt, vb);
+    if (flags) st_flag(flags + i, uint8_t(r));
+    if (evout) evout[i] = ev;
+    n_ev += ev;
+    if (r == EV_OK) n_ok++; else n_fail++;
+  }
+  block_add(&d.ctrl->occupancy, n_ok);
+  block_add(&d.ctrl->insert_ok, n_ok);
+  block_add(&d.ctrl->insert_fail, n_fail);
+  block_add(&d.ctrl->evictions, n_ev);
+  block_add(&d.ctrl->rollbacks, ec.rollbacks);
+  block_add(&d.ctrl->rollback_lost, ec.rollback_lost);
+  block_add(&d.ctrl->contention, ec.contention);
+  if (ec.contention) atomicOr(&d.ctrl->error_word, 1u);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&d.ctrl->done_blocks, 1u);
+    if (prev == gridDim.x - 1) {
+      d.ctrl->queue_count = 0;
+      d.ctrl->done_blocks = 0;
+      __threadfence();
+    }
+  }
+}
+
+// The whole insert of Alg. 1 + Sec. 4.6.1, one thread, keys in order
+// (deterministic placement; used to compare with a sequential
+// implementation bit for bit).
+template <class G>
+__global__ void k_insert_serial(DevFilter d, const uint64_t* __restrict__ keys,
+                                uint64_t n, uint8_t* __restrict__ flags,
+                                uint32_t* __restrict__ evout) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  EvictCounters ec;
+  unsigned long long n_ok = 0, n_fail = 0, n_ev = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const KeyHash kh = hash_key<G>(d, keys[i]);
+    uint32_t ev = 0, vt = 0;
+    uint64_t vb = 0;
+    int r;
+    const int a = try_insert<G>(d, kh.i1, kh.fp);
+    if (a == TI_OK) {
+      r = EV_OK;
+    } else if (a == TI_CONTENTION) {
+      r = EV_CONTENTION;
+      vt = kh.fp;
+      vb = kh.i1;
+    } else {
+      const int b = try_insert<G>(d, kh.i2, kh.fp | G::kChoice);
+      if (b == TI_OK) {
+        r = EV_OK;
+      } else if (b == TI_CONTENTION) {
+        r = EV_CONTENTION;
+        vt = kh.fp | G::kChoice;
+        vb = kh.i2;
+      } else {
+        r = evict_key<G>(d, kh, ev, vt, vb, ec);
+      }
+    }
+    if (r != EV_OK) log_victim(d, vt, vb);
+    if (flags) flags[i] = uint8_t(r);
+    if (evout) evout[i] = ev;
+    n_ev += ev;
+    if (r == EV_OK) n_ok++; else n_fail++;
+  }
+  atomicAdd(&d.ctrl->occupancy, n_ok);
+  atomicAdd(&d.ctrl->insert_ok, n_ok);
+  atomicAdd(&d.ctrl->insert_fail, n_fail);
+  atomicAdd(&d.ctrl->evictions, n_ev);
+  atomicAdd(&d.ctrl->rollbacks, (unsigned long long)ec.rollbacks);
+  atomicAdd(&d.ctrl->rollback_lost, (unsigned long long)ec.rollback_lost);
+  atomicAdd(&d.ctrl->contention, (unsigned long long)ec.contention);
+}
+
+// ---------------------------------------------------------------------------
+// Query (Alg. 2): Find(i1) or Find(i2).  All K first-bucket loads of a
+// thread are issued together; the second buckets are loaded only for the
+// keys not found in the first (the short-circuit of Alg. 2).  Whole buckets
+// are loaded with single vector loads (up to 256 bits), so the scan order
+// of Alg. 2 does not matter: any word matching decides.
+// ---------------------------------------------------------------------------
+template <class G, int K>
+__global__ void __launch_bounds__(kBlock)
+k_contains(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
+           uint8_t* __restrict__ flags) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K)) {
+    bool valid[K], hit[K];
+    KeyHash kh[K];
+    Bucket<G> bk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint64_t i = base + uint64_t(k) * 32 + lane;
+      valid[k] = i < n;
+      kh[k] = hash_key<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (valid[k]) bk[k] = load_bucket<G, true>(bucket_ptr<G>(d, kh[k].i1));
+#pragma unroll
+    for (int k = 0; k < K; ++k) hit[k] = valid[k] && bucket_has<G>(bk[k], kh[k].fp);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (valid[k] && !hit[k])
+        bk[k] = load_bucket<G, true>(bucket_ptr<G>(d, kh[k].i2));
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (valid[k] && !hit[k]) hit[k] = bucket_has<G>(bk[k], kh[k].fp | G::kChoice);
+    if (flags) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (valid[k]) st_flag(flags + base + uint64_t(k) * 32 + lane, hit[k] ? 1 : 0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Delete (Alg. 3): TryRemove(i1) or TryRemove(i2), K keys per thread with
+// their CASes issued together.
+// ---------------------------------------------------------------------------
+template <class G, int K>
+__global__ void __launch_bounds__(kBlock)
+k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
+         uint8_t* __restrict__ flags) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t n_ok = 0, n_fail = 0, n_cont = 0;
+  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K)) {
+    bool valid[K];
+    KeyHash kh[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint64_t i = base + uint64_t(k) * 32 + lane;
+      valid[k] = i < n;
+      kh[k] = hash_key<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
+    }
+    uint64_t bkt[K];
+    uint32_t tag[K];
+    int r1[K], r2[K];
+    bool act[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      bkt[k] = kh[k].i1;
+      tag[k] = kh[k].fp;
+      act[k] = valid[k];
+    }
+    cas_many<G, K, false>(d, bkt, tag, act, r1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      bkt[k] = kh[k].i2;
+      tag[k] = kh[k].fp | G::kChoice;
+      act[k] = valid[k] && r1[k] == TI_FULL;
+    }
+    cas_many<G, K, false>(d, bkt, tag, act, r2);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!valid[k]) continue;
+      int r;
+      if (r1[k] == TI_OK || (r1[k] == TI_FULL && r2[k] == TI_OK)) {
+        r = 1;
+        n_ok++;
+      } else if (r1[k] == TI_CONTENTION || r2[k] == TI_CONTENTION) {
+        r = 2;
+        n_cont++;
+      } else {
+        r = 0;
+        n_fail++;
+      }
+      if (flags) st_flag(flags + base + uint64_t(k) * 32 + lane, uint8_t(r));
+    }
+  }
+  block_add(&d.ctrl->occupancy, n_ok, /*negate=*/true);
+  block_add(&d.ctrl->remove_ok, n_ok);
+  block_add(&d.ctrl->remove_fail, n_fail + n_cont);
+  block_add(&d.ctrl->contention, n_cont);
+}
+
+// Hash export for tests: fp, i1, i2 per key.
+template <class G>
+__global__ void k_hash(DevFilter d, const uint64_t* __restrict__ keys,
+                       uint64_t n, uint32_t* fp, uint64_t* i1, uint64_t* i2) {
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    const KeyHash kh = hash_key<G>(d, keys[i]);
+    if (fp) fp[i] = kh.fp;
+    if (i1) i1[i] = kh.i1;
+    if (i2) i2[i] = kh.i2;
+  }
+}
+
+// Number of nonzero slots, added to *out.
+template <class G>
+__global__ void __launch_bounds__(kBlock)
+k_count(DevFilter d, unsigned long long* out) {
+  using W = typename G::Word;
+  const W* t = reinterpret_cast<const W*>(d.table);
+  const uint64_t words = d.m * G::kWpb;
+  uint32_t c = 0;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < words;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    const W w = t[i];
+    if constexpr (G::kW32)
+      c += G::kTpw - __popc(zero_lanes<G>(w));
+    else
+      c += G::kTpw - __popcll(zero_lanes<G>(w));
+  }
+  block_add(out, c);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+int device_sm_count();
+int cached_occupancy(const void* fn, int block);
+
+template <class F>
+inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
+  const int occ = cached_occupancy(reinterpret_cast<const void*>(fn), kBlock);
+  const uint64_t cap = uint64_t(device_sm_count()) * uint64_t(occ > 0 ? occ : 1);
+  uint64_t need = (work_items + per_block - 1) / per_block;
+  if (need < 1) need = 1;
+  return unsigned(need < cap ? need : cap);
+}
+
+template <class G>
+struct Launch {
+  static constexpr int K = Tiles<G>::K;
+
+  static cudaError_t contains(const DevFilter& d, const uint64_t* keys,
+                              uint64_t n, uint8_t* flags, cudaStream_t s) {
+    auto fn = k_contains<G, K>;
+    fn<<<persistent_grid(fn, n, kBlock * K), kBlock, 0, s>>>(d, keys, n, flags);
+    return cudaGetLastError();
+  }
+  static cudaError_t remove(const DevFilter& d, const uint64_t* keys,
+                            uint64_t n, uint8_t* flags, cudaStream_t s) {
+    auto fn = k_remove<G, K>;
+    fn<<<persistent_grid(fn, n, kBlock * K), kBlock, 0, s>>>(d, keys, n, flags);
+    return cudaGetLastError();
+  }
+  static cudaError_t insert_chunk(const DevFilter& d, const uint64_t* keys,
+                                  uint32_t n, uint8_t* flags, uint32_t* evout,
+                                  uint32_t* queue, cudaStream_t s) {
+    auto f1 = k_insert_direct<G, K>;
+    f1<<<persistent_grid(f1, n, kBlock * K), kBlock, 0, s>>>(d, keys, n, flags,
+                                                             evout, queue);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto f2 = k_insert_evict<G>;
+    const int occ = cached_occupancy(reinterpret_cast<const void*>(f2), kBlock);
+    f2<<<unsigned(device_sm_count() * (occ > 0 ? occ : 1)), kBlock, 0, s>>>(
+        d, keys, flags, evout, queue);
+    return cudaGetLastError();
+  }
+  static cudaError_t insert_serial(const DevFilter& d, const uint64_t* keys,
+                                   uint64_t n, uint8_t* flags, uint32_t* evout,
+                                   cudaStream_t s) {
+    k_insert_serial<G><<<1, 32, 0, s>>>(d, keys, n, flags, evout);
+    return cudaGetLastError();
+  }
+  static cudaError_t hash(const DevFilter& d, const uint64_t* keys, uint64_t n,
+                          uint32_t* fp, uint64_t* i1, uint64_t* i2,
+                          cudaStream_t s) {
+    auto fn = k_hash<G>;
+    fn<<<persistent_grid(fn, n, kBlock), kBlock, 0, s>>>(d, keys, n, fp, i1, i2);
+    return cudaGetLastError();
+  }
+  static cudaError_t count(const DevFilter& d, unsigned long long* out,
+                           cudaStream_t s) {
+    auto fn = k_count<G>;
+    fn<<<persistent_grid(fn, d.m * G::kWpb, kBlock), kBlock, 0, s>>>(d, out);
+    return cudaGetLastError();
+  }
+};
+
+struct Ops {
+  cudaError_t (*contains)(const DevFilter&, const uint64_t*, uint64_t,
+                          uint8_t*, cudaStream_t);
+  cudaError_t (*remove)(const DevFilter&, const uint64_t*, uint64_t, uint8_t*,
+                        cudaStream_t);
+  cudaError_t (*insert_chunk)(const DevFilter&, const uint64_t*, uint32_t,
+                              uint8_t*, uint32_t*, uint32_t*, cudaStream_t);
+  cudaError_t (*insert_serial)(const DevFilter&, const uint64_t*, uint64_t,
+                               uint8_t*, uint32_t*, cudaStream_t);
+  cudaError_t (*hash)(const DevFilter&, const uint64_t*, uint64_t, uint32_t*,
+                      uint64_t*, uint64_t*, cudaStream_t);
+  cudaError_t (*count)(const DevFilter&, unsigned long long*, cudaStream_t);
+};
+
+template <class G>
+const Ops* ops_for() {
+  static const Ops o = {&Launch<G>::contains, &Launch<G>::remove,
+                        &Launch<G>::insert_chunk, &Launch<G>::insert_serial,
+                        &Launch<G>::hash, &Launch<G>::count};
+  return &o;
+}
+
+// One per translation unit (fingerprint width).
+const Ops* ops_f8(int b, int policy);
+const Ops* ops_f16(int b, int policy);
+const Ops* ops_f32(int b, int policy);
+
+inline const Ops* get_ops(int f, int b, int policy) {
+  switch (f) {
+    case 8: return ops_f8(b, policy);
+    case 16: return ops_f16(b, policy);
+    case 32: return ops_f32(b, policy);
+    default: return nullptr;
+  }
+}
+
+}  // namespace cfk

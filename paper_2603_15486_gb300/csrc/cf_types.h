@@ -1,0 +1,51 @@
+// Types shared by the kernels and the host side of libcf.
+#pragma once
+
+#include <cstdint>
+
+namespace cfk {
+
+// Device control block: counters of one filter (256 bytes, at the start of
+// the filter's device memory).
+struct Ctrl {
+  unsigned long long occupancy;
+  unsigned long long insert_ok;
+  unsigned long long insert_fail;
+  unsigned long long remove_ok;
+  unsigned long long remove_fail;
+  unsigned long long evictions;
+  unsigned long long victims;
+  unsigned long long rollbacks;
+  unsigned long long rollback_lost;
+  unsigned long long contention;
+  unsigned int error_word;
+  unsigned int queue_count;  // eviction work queue fill (insert scratch)
+  unsigned int done_blocks;  // last-block-done counter of the evict kernel
+  unsigned int pad0;
+  unsigned long long scratch_count;  // for cf_count_occupied
+  unsigned long long pad[19];
+};
+static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
+
+struct Victim {
+  uint32_t tag;
+  uint32_t pad;
+  uint64_t bucket;
+};
+
+// Everything a kernel needs to address one filter (passed by value).
+struct DevFilter {
+  void* table;
+  uint64_t m;       // buckets
+  uint64_t mask;    // m - 1 (XOR policy)
+  uint64_t fm_m;    // fastmod multiplier for m   (Offset policy)
+  uint64_t fm_m1;   // fastmod multiplier for m-1 (Offset policy)
+  Ctrl* ctrl;
+  Victim* victims;
+  uint32_t victim_cap;
+  uint32_t max_ev;
+  uint32_t eviction;  // 0 BFS, 1 DFS
+  uint32_t pad;
+};
+
+}  // namespace cfk

@@ -1,0 +1,275 @@
+"""Python binding of libcf: argument marshalling only.
+
+Every operation is one call into the C ABI (include/cf.h); every step of the
+insert / query / delete path runs in the library's CUDA kernels.  PyTorch
+supplies device memory (tensors) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CfConfig, CfStats, check
+
+POLICIES = {"xor": 0, "offset": 1}
+EVICTIONS = {"bfs": 0, "dfs": 1}
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+def _dev_keys(keys: torch.Tensor) -> torch.Tensor:
+    if not isinstance(keys, torch.Tensor) or not keys.is_cuda:
+        raise TypeError("keys must be a CUDA tensor (use *_host for host keys)")
+    if keys.dtype not in (torch.int64, torch.uint64):
+        raise TypeError(f"keys must be int64/uint64, got {keys.dtype}")
+    if not keys.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    return keys
+
+
+def _dev_out(out, n: int, dtype, device) -> torch.Tensor:
+    if out is None:
+        return torch.empty(n, dtype=dtype, device=device)
+    if not out.is_cuda or out.dtype != dtype or out.numel() < n or not out.is_contiguous():
+        raise ValueError(f"output must be a contiguous CUDA {dtype} tensor of >= {n}")
+    return out
+
+
+def make_config(num_buckets: int, fp_bits: int = 16, slots_per_bucket: int = 4,
+                max_evictions: int = 500, policy: str = "xor",
+                eviction: str = "bfs", victim_capacity: int = 0) -> CfConfig:
+    return CfConfig(int(num_buckets), int(fp_bits), int(slots_per_bucket),
+                    int(max_evictions), POLICIES[policy], EVICTIONS[eviction],
+                    int(victim_capacity))
+
+
+def required_bytes(**kw) -> int:
+    cfg = make_config(**kw)
+    return int(_lib.load().cf_required_bytes(ctypes.byref(cfg)))
+
+
+class CuckooFilter:
+    """A cuckoo filter on the current CUDA device.
+
+    ``memory``: optional caller-owned CUDA uint8 tensor of at least
+    ``required_bytes(...)`` bytes (cf_create_at); otherwise the library
+    allocates (cf_create_ex)."""
+
+    def __init__(self, num_buckets: int, fp_bits: int = 16, slots_per_bucket: int = 4,
+                 max_evictions: int = 500, policy: str = "xor", eviction: str = "bfs",
+                 victim_capacity: int = 0, memory: Optional[torch.Tensor] = None):
+        self._L = _lib.load()
+        self.cfg = make_config(num_buckets, fp_bits, slots_per_bucket, max_evictions,
+                               policy, eviction, victim_capacity)
+        self.num_buckets, self.fp_bits, self.slots_per_bucket = (
+            int(num_buckets), int(fp_bits), int(slots_per_bucket))
+        self.max_evictions, self.policy, self.eviction = max_evictions, policy, eviction
+        h = ctypes.c_void_p()
+        self._memory = memory
+        if memory is None:
+            check(self._L.cf_create_ex(ctypes.byref(self.cfg), ctypes.byref(h)),
+                  "cf_create_ex")
+        else:
+            if not memory.is_cuda or memory.dtype != torch.uint8:
+                raise TypeError("memory must be a CUDA uint8 tensor")
+            check(self._L.cf_create_at(memory.data_ptr(), memory.numel(),
+                                       ctypes.byref(self.cfg), ctypes.byref(h)),
+                  "cf_create_at")
+        self._h = h
+        self.device = torch.cuda.current_device()
+
+    # ---- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.cf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    @property
+    def table_bytes(self) -> int:
+        return self.num_buckets * self.slots_per_bucket * self.fp_bits // 8
+
+    @property
+    def capacity(self) -> int:
+        return self.num_buckets * self.slots_per_bucket
+
+    # ---- hot path ------------------------------------------------------------
+    def insert(self, keys: torch.Tensor, flags: Optional[torch.Tensor] = None,
+               evictions: Optional[torch.Tensor] = None, stream=None,
+               want_flags: bool = True) -> Optional[torch.Tensor]:
+        keys = _dev_keys(keys)
+        n = keys.numel()
+        fl = _dev_out(flags, n, torch.uint8, keys.device) if (want_flags or flags is not None) else None
+        ev = None
+        if evictions is not None:
+            ev = _dev_out(evictions, n, torch.int32, keys.device)
+        check(self._L.cf_insert_ex(self._h, keys.data_ptr(), n,
+                                   fl.data_ptr() if fl is not None else None,
+                                   ev.data_ptr() if ev is not None else None,
+                                   _stream_handle(stream)), "cf_insert")
+        return fl
+
+    def contains(self, keys: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+        keys = _dev_keys(keys)
+        out = _dev_out(out, keys.numel(), torch.uint8, keys.device)
+        check(self._L.cf_contains(self._h, keys.data_ptr(), keys.numel(),
+                                  out.data_ptr(), _stream_handle(stream)), "cf_contains")
+        return out
+
+    def remove(self, keys: torch.Tensor, out: Optional[torch.Tensor] = None,
+               stream=None, want_flags: bool = True) -> Optional[torch.Tensor]:
+        keys = _dev_keys(keys)
+        fl = _dev_out(out, keys.numel(), torch.uint8, keys.device) if (want_flags or out is not None) else None
+        check(self._L.cf_remove(self._h, keys.data_ptr(), keys.numel(),
+                                fl.data_ptr() if fl is not None else None,
+                                _stream_handle(stream)), "cf_remove")
+        return fl
+
+    def insert_serial(self, keys: torch.Tensor, evictions: bool = True, stream=None):
+        keys = _dev_keys(keys)
+        n = keys.numel()
+        fl = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        ev = torch.empty(n, dtype=torch.int32, device=keys.device) if evictions else None
+        check(self._L.cf_debug_insert_serial(self._h, keys.data_ptr(), n, fl.data_ptr(),
+                                             ev.data_ptr() if ev is not None else None,
+                                             _stream_handle(stream)), "cf_debug_insert_serial")
+        return fl, ev
+
+    # ---- host-buffer forms (end to end) ---------------------------------------
+    @staticmethod
+    def _host(a, dtype) -> np.ndarray:
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                raise TypeError("host buffers expected")
+            return a
+        return np.ascontiguousarray(a, dtype=dtype)
+
+    def _host_call(self, fn, keys, out, what, stream, need_out=True):
+        k = self._host(keys, np.uint64)
+        n = k.numel() if isinstance(k, torch.Tensor) else k.size
+        if out is None and need_out:
+            out = np.empty(n, np.uint8)
+        kp = k.data_ptr() if isinstance(k, torch.Tensor) else k.ctypes.data
+        op = None if out is None else (out.data_ptr() if isinstance(out, torch.Tensor)
+                                       else out.ctypes.data)
+        check(fn(self._h, kp, n, op, _stream_handle(stream)), what)
+        return out
+
+    def insert_host(self, keys, out=None, stream=None):
+        return self._host_call(self._L.cf_insert_host, keys, out, "cf_insert_host", stream)
+
+    def contains_host(self, keys, out=None, stream=None):
+        return self._host_call(self._L.cf_contains_host, keys, out, "cf_contains_host", stream)
+
+    def remove_host(self, keys, out=None, stream=None):
+        return self._host_call(self._L.cf_remove_host, keys, out, "cf_remove_host", stream)
+
+    def set_staging_chunk(self, keys_per_chunk: int):
+        check(self._L.cf_set_staging_chunk(self._h, int(keys_per_chunk)), "cf_set_staging_chunk")
+
+    # ---- state -----------------------------------------------------------------
+    def clear(self, stream=None):
+        check(self._L.cf_clear(self._h, _stream_handle(stream)), "cf_clear")
+
+    def stats(self, stream=None) -> dict:
+        st = CfStats()
+        check(self._L.cf_stats(self._h, ctypes.byref(st), _stream_handle(stream)), "cf_stats")
+        return {n: int(getattr(st, n)) for n, _ in CfStats._fields_}
+
+    def victims(self, stream=None):
+        cnt = ctypes.c_uint64()
+        check(self._L.cf_victims(self._h, None, None, 0, ctypes.byref(cnt),
+                                 _stream_handle(stream)), "cf_victims")
+        n = cnt.value
+        tags = np.empty(n, np.uint32)
+        buckets = np.empty(n, np.uint64)
+        if n:
+            check(self._L.cf_victims(self._h, tags.ctypes.data, buckets.ctypes.data, n,
+                                     ctypes.byref(cnt), _stream_handle(stream)), "cf_victims")
+        return tags, buckets
+
+    def snapshot_bytes(self) -> int:
+        return int(self._L.cf_snapshot_bytes(self._h))
+
+    def snapshot(self, device: bool = False, stream=None):
+        """64-byte header + raw table; numpy (host) or a CUDA uint8 tensor."""
+        n = self.snapshot_bytes()
+        if device:
+            buf = torch.empty(n, dtype=torch.uint8, device="cuda")
+            check(self._L.cf_snapshot(self._h, buf.data_ptr(), n, 1,
+                                      _stream_handle(stream)), "cf_snapshot")
+            return buf
+        buf = np.empty(n, np.uint8)
+        check(self._L.cf_snapshot(self._h, buf.ctypes.data, n, 0, _stream_handle(stream)),
+              "cf_snapshot")
+        return buf
+
+    def load(self, snap, stream=None):
+        if isinstance(snap, torch.Tensor) and snap.is_cuda:
+            check(self._L.cf_load(self._h, snap.data_ptr(), snap.numel(), 1,
+                                  _stream_handle(stream)), "cf_load")
+        else:
+            buf = np.ascontiguousarray(snap, dtype=np.uint8)
+            check(self._L.cf_load(self._h, buf.ctypes.data, buf.size, 0,
+                                  _stream_handle(stream)), "cf_load")
+
+    def count_occupied(self, stream=None) -> int:
+        v = ctypes.c_uint64()
+        check(self._L.cf_count_occupied(self._h, ctypes.byref(v), _stream_handle(stream)),
+              "cf_count_occupied")
+        return v.value
+
+    def table_view(self) -> torch.Tensor:
+        """The live device table as a uint8 tensor (no copy; do not write)."""
+        ptr = self._L.cf_table_ptr(self._h)
+        return _device_bytes(ptr, self.table_bytes, self)
+
+
+class _Owner:
+    pass
+
+
+def _device_bytes(ptr: int, nbytes: int, owner) -> torch.Tensor:
+    """Wrap a raw device pointer as a CUDA uint8 tensor (kept alive by owner)."""
+    class _CAI:
+        def __init__(self):
+            self.__cuda_array_interface__ = {
+                "shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                "version": 3, "strides": None}
+    t = torch.as_tensor(_CAI(), device="cuda")
+    t._cf_owner = owner  # noqa: SLF001
+    return t
+
+
+def hash_debug(keys: torch.Tensor, fp_bits: int, num_buckets: int, policy: str = "xor",
+               stream=None):
+    L = _lib.load()
+    keys = _dev_keys(keys)
+    n = keys.numel()
+    fp = torch.empty(n, dtype=torch.int32, device=keys.device)
+    i1 = torch.empty(n, dtype=torch.int64, device=keys.device)
+    i2 = torch.empty(n, dtype=torch.int64, device=keys.device)
+    check(L.cf_hash_debug(keys.data_ptr(), n, fp_bits, num_buckets, POLICIES[policy],
+                          fp.data_ptr(), i1.data_ptr(), i2.data_ptr(),
+                          _stream_handle(stream)), "cf_hash_debug")
+    return fp, i1, i2

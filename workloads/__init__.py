@@ -22,7 +22,11 @@ from .gen import (  # noqa: F401
     query_mix_dev,
 )
 from .configs import (  # noqa: F401
+    BY_NAME,
     LARGE,
+    MEDIUM,
+    REF_STEP,
+    SCALE,
     SINGLE,
     Workload,
     lf_count,

@@ -62,3 +62,22 @@ SINGLE = Workload(name="single_2^18x4_f16", m=1 << 18, f=16, b=4,
 LARGE = Workload(name="large_2^28x4_f16_lf0.95", m=1 << 28, f=16, b=4,
                  max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
                  n_queries=1 << 30, query_pos_seed=12, n_deletes=1 << 28)
+
+# The same structure at 2^24 buckets (128 MiB table, larger than L2): the
+# profiling-size case of the large filter.
+MEDIUM = Workload(name="medium_2^24x4_f16_lf0.95", m=1 << 24, f=16, b=4,
+                  max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
+                  n_queries=1 << 26, query_pos_seed=12, n_deletes=1 << 24)
+
+# The CPU scale model of the large filter (2^22 buckets): same load-factor
+# path, query mix and delete fraction; used to time the oracle and to count
+# the buckets each operation touches.
+SCALE = Workload(name="scale_2^22x4_f16_lf0.95", m=1 << 22, f=16, b=4,
+                 max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
+                 n_queries=1 << 24, query_pos_seed=12, n_deletes=1 << 22)
+
+REF_STEP = Workload(name="ref_2^20x4_f16_lf0.95", m=1 << 20, f=16, b=4,
+                    max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
+                    n_queries=1 << 22, query_pos_seed=12, n_deletes=1 << 20)
+
+BY_NAME = {w.name: w for w in (SINGLE, LARGE, MEDIUM, SCALE, REF_STEP)}
