@@ -26,12 +26,29 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _elf_matches_host(path: str) -> bool:
+    """True if `path` is an ELF file built for this machine's architecture
+    (x86-64 objects can travel to an Arm host with the source tree)."""
+    import platform
+    want = {"x86_64": 0x3E, "amd64": 0x3E, "aarch64": 0xB7, "arm64": 0xB7}.get(
+        platform.machine().lower())
+    try:
+        with open(path, "rb") as fh:
+            hdr = fh.read(20)
+    except OSError:
+        return False
+    if len(hdr) < 20 or hdr[:4] != b"\x7fELF":
+        return False
+    return want is None or int.from_bytes(hdr[18:20], "little") == want
+
+
 def build(force: bool = False) -> str:
     """Compile ``cf_oracle.c`` into ``liboracle.so`` next to it (plain gcc,
     no architecture-specific flags, so it builds the same on x86 and Arm)."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(_SRC[:-1] + "h"))):
+                                              os.path.getmtime(_SRC[:-1] + "h"))
+            and _elf_matches_host(_LIB)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.run(["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared",

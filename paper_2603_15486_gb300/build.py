@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -16,12 +17,27 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libcf.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
+
+
+def _elf_matches_host(path: str) -> bool:
+    """True if `path` is an ELF file built for this machine's architecture
+    (x86-64 objects can travel to an Arm host with the source tree)."""
+    want = {"x86_64": 0x3E, "amd64": 0x3E, "aarch64": 0xB7, "arm64": 0xB7}.get(
+        platform.machine().lower())
+    try:
+        with open(path, "rb") as fh:
+            hdr = fh.read(20)
+    except OSError:
+        return False
+    if len(hdr) < 20 or hdr[:4] != b"\x7fELF":
+        return False
+    return want is None or int.from_bytes(hdr[18:20], "little") == want
 
 
 def nvcc() -> str:
@@ -40,7 +56,8 @@ def _headers():
 def _compile(src: str, extra=()):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
-    if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
+    if (os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep
+            and _elf_matches_host(obj)):
         return obj
     tmp = obj + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", tmp]
@@ -60,7 +77,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(_compile, srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest
+            and _elf_matches_host(LIB)):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

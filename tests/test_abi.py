@@ -23,9 +23,12 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2603_15486_gb300 import build
-    path = build.build()
-    return ctypes.CDLL(path)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_cf_build", os.path.join(ROOT, "paper_2603_15486_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return ctypes.CDLL(mod.build())
 
 
 def test_header_declares_the_hot_path():

@@ -24,10 +24,27 @@ def _nvcc() -> str:
     return "nvcc"
 
 
+def _elf_matches_host(path: str) -> bool:
+    """True if `path` is an ELF file built for this machine's architecture
+    (x86-64 objects can travel to an Arm host with the source tree)."""
+    import platform
+    want = {"x86_64": 0x3E, "amd64": 0x3E, "aarch64": 0xB7, "arm64": 0xB7}.get(
+        platform.machine().lower())
+    try:
+        with open(path, "rb") as fh:
+            hdr = fh.read(20)
+    except OSError:
+        return False
+    if len(hdr) < 20 or hdr[:4] != b"\x7fELF":
+        return False
+    return want is None or int.from_bytes(hdr[18:20], "little") == want
+
+
 def build(force: bool = False) -> str:
     """Compile ``gen.cu`` into ``libcfwl.so`` in-tree for sm_103a."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
+            and _elf_matches_host(_LIB)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.run([_nvcc(), *NVCC_ARCH, "-O3", "-lineinfo", "-std=c++17",
