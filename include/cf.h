@@ -201,6 +201,25 @@ cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
                                  uint64_t n, uint8_t* out_flags,
                                  uint32_t* evictions_out, void* stream);
 
+/* ---- measurement helpers ------------------------------------------------ */
+/* Random-gather ceiling: n_access independent loads of access_bytes (8, 16
+ * or 32) at pseudo-random aligned offsets within the first power-of-two
+ * part of the device buffer `buf` (32-byte aligned), with the load
+ * instructions of the query kernel, loads_per_thread (4, 8 or 16) in
+ * flight per thread.  Asynchronous; `sink` is a device uint64 the kernel
+ * may write.  Time it with events on `stream` to get random loads/s. */
+cf_status cf_probe_gather(const void* buf, uint64_t bytes, uint64_t n_access,
+                          uint32_t access_bytes, uint32_t loads_per_thread,
+                          uint64_t seed, unsigned long long* sink,
+                          void* stream);
+/* The CUDA context limit cudaLimitMaxL2FetchGranularity of the current
+ * device (0..128 bytes): how much L2 fetches from DRAM around a missed
+ * sector.  Random bucket probes use one 32-byte sector; a larger fetch
+ * moves bytes nobody reads.  Process-wide for the current context; it
+ * does not outlive the process. */
+cf_status cf_set_l2_fetch_granularity(uint32_t bytes);
+cf_status cf_get_l2_fetch_granularity(uint32_t* bytes);
+
 const char* cf_status_str(cf_status s);
 /* Text of the last error seen by a cf_* call on this host thread. */
 const char* cf_last_error(void);

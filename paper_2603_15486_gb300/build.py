@@ -23,6 +23,8 @@ LIB = os.path.join(HERE, "libcf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
+# Extra nvcc flags for tuning builds (e.g. "-DCF_K_MUT=4 -DCF_MINB_MUT=3").
+FLAGS += os.environ.get("CF_EXTRA_NVCC", "").split()
 
 
 def _elf_matches_host(path: str) -> bool:

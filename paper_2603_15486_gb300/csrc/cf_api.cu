@@ -14,18 +14,19 @@
 #include <unordered_map>
 
 #include "cf.h"
+#include "cf_internal.h"
 #include "cf_kernels.cuh"
 
 using cfk::Ctrl;
 using cfk::DevFilter;
 using cfk::Victim;
+using cfk::Stage;
 
 namespace {
 
 constexpr uint64_t kInsertChunk = 1ull << 28;  // keys per insert launch pair
 constexpr uint32_t kDefaultVictims = 4096;
 constexpr uint32_t kMaxVictims = 1u << 26;
-constexpr uint64_t kDefaultStage = 1ull << 24;
 
 thread_local char g_err[256] = "";
 
@@ -92,36 +93,11 @@ DevFilter make_dev(const cf_config* c, char* mem) {
   return d;
 }
 
-struct Stage {
-  uint64_t* keys = nullptr;
-  uint8_t* flags = nullptr;
-  cudaEvent_t in_done = nullptr, comp_done = nullptr, out_done = nullptr;
-};
-
 std::mutex g_mu;
 std::unordered_map<int, int> g_sms;
 std::unordered_map<const void*, int> g_occ[64];
 
 }  // namespace
-
-struct cf_filter {
-  cf_config cfg{};
-  int device = 0;
-  char* mem = nullptr;
-  size_t mem_bytes = 0;
-  bool owns = false;
-  DevFilter d{};
-  const cfk::Ops* ops = nullptr;
-  cudaEvent_t last_ev = nullptr;
-  cudaStream_t last_stream = nullptr;
-  bool has_last = false;
-  uint32_t* queue = nullptr;
-  uint64_t queue_cap = 0;
-  uint64_t stage_chunk = kDefaultStage;
-  Stage stage[2];
-  cudaStream_t s_in = nullptr, s_out = nullptr;
-  bool stage_ready = false;
-};
 
 namespace cfk {
 
@@ -154,22 +130,52 @@ int cached_occupancy(const void* fn, int block) {
   return occ;
 }
 
-}  // namespace cfk
-
-namespace {
-
 cf_status order_on(cf_filter* f, cudaStream_t s) {
-  if (f->has_last && f->last_stream != s)
-    CF_CUDA(cudaStreamWaitEvent(s, f->last_ev, 0));
+  if (f->has_last && f->last_stream != s) {
+    cudaEvent_t ev = f->ext_ev ? f->ext_ev : f->last_ev;
+    cudaError_t e = cudaStreamWaitEvent(s, ev, 0);
+    if (e != cudaSuccess) {
+      set_error("cudaStreamWaitEvent", e);
+      return CF_ECUDA;
+    }
+  }
   return CF_OK;
 }
 
 cf_status mark(cf_filter* f, cudaStream_t s) {
-  CF_CUDA(cudaEventRecord(f->last_ev, s));
+  cudaError_t e = cudaEventRecord(f->last_ev, s);
+  if (e != cudaSuccess) {
+    set_error("cudaEventRecord", e);
+    return CF_ECUDA;
+  }
+  f->ext_ev = nullptr;
   f->last_stream = s;
   f->has_last = true;
   return CF_OK;
 }
+
+void mark_external(cf_filter* f, cudaStream_t s, cudaEvent_t ev) {
+  f->ext_ev = ev;
+  f->last_stream = s;
+  f->has_last = true;
+}
+
+cudaEvent_t pooled_event() {
+  // Events handed to filters by batched launches live until process exit.
+  cudaEvent_t ev = nullptr;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  return ev;
+}
+
+void set_error(const char* what, cudaError_t e) { set_err(what, e); }
+void set_error_text(const char* text) { snprintf(g_err, sizeof g_err, "%s", text); }
+
+}  // namespace cfk
+
+namespace {
+
+using cfk::mark;
+using cfk::order_on;
 
 cf_status ensure_queue(cf_filter* f, uint64_t keys) {
   const uint64_t want = keys < kInsertChunk ? keys : kInsertChunk;
@@ -418,7 +424,7 @@ cf_status cf_create_at(void* dev_mem, size_t bytes, const cf_config* cfg,
 
 cf_status cf_destroy(cf_filter* f) {
   if (!f) return CF_OK;
-  if (f->has_last) cudaEventSynchronize(f->last_ev);
+  if (f->has_last) cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev);
   free_staging(f);
   if (f->queue) cudaFree(f->queue);
   if (f->last_ev) cudaEventDestroy(f->last_ev);
@@ -476,7 +482,7 @@ cf_status cf_remove_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
 cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk) {
   if (!f || keys_per_chunk == 0 || keys_per_chunk > kInsertChunk)
     return CF_EINVAL;
-  if (f->has_last) cudaEventSynchronize(f->last_ev);
+  if (f->has_last) cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev);
   free_staging(f);
   f->stage_chunk = keys_per_chunk;
   return CF_OK;

@@ -146,6 +146,14 @@ __device__ __forceinline__ typename G::Word select_word(const Bucket<G>& b,
   return w;
 }
 
+template <class G>
+__device__ __forceinline__ void set_word(Bucket<G>& b, int wi,
+                                         typename G::Word v) {
+#pragma unroll
+  for (int q = 0; q < G::kWpb; ++q)
+    if (q == wi) b.w[q] = v;
+}
+
 // ---------------------------------------------------------------------------
 // SWAR on one word (Alg. 1-3 "ZeroMask", "HasZeroSegment", "BroadcastTag").
 // zero_lanes sets the top bit of exactly the lanes that are zero: adding
@@ -240,9 +248,11 @@ __device__ __forceinline__ uint64_t fastmod32(uint32_t x, uint64_t M,
   return __umul64hi(M * uint64_t(x), d);
 }
 
+// Bucket indices fit in 32 bits (m <= 2^32), which halves the registers a
+// thread needs per key in flight.
 struct KeyHash {
   uint64_t h;
-  uint64_t i1, i2;
+  uint32_t i1, i2;
   uint32_t fp;  // fingerprint proper (without the choice bit)
 };
 
@@ -251,20 +261,41 @@ __device__ __forceinline__ uint64_t offset_of(const DevFilter& d, uint32_t fp) {
   return 1u + fastmod32(fp_hash(fp), d.fm_m1, d.m - 1);
 }
 
+// The alternate bucket of a key (Eq. 3 / Sec. 4.6.2) from its primary
+// bucket and fingerprint.  Kernels call it only for keys that need i2.
 template <class G>
-__device__ __forceinline__ KeyHash hash_key(const DevFilter& d, uint64_t key) {
+__device__ __forceinline__ uint32_t alt_index(const DevFilter& d, uint32_t i1,
+                                              uint32_t fp) {
+  if constexpr (G::POLICY == 0) {
+    return i1 ^ (fp_hash(fp) & uint32_t(d.mask));
+  } else {
+    const uint64_t j = uint64_t(i1) + offset_of<G>(d, fp);
+    return uint32_t(j >= d.m ? j - d.m : j);
+  }
+}
+
+// Fingerprint and primary bucket (Sec. 4.3 step 1): the upper 32 bits of
+// the hash give the fingerprint (0 is EMPTY, so 0 becomes 1), the lower 32
+// bits the primary bucket.
+template <class G>
+__device__ __forceinline__ KeyHash hash_primary(const DevFilter& d,
+                                                uint64_t key) {
   KeyHash k;
   k.h = xxh64_u64(key);
-  uint32_t raw = uint32_t(k.h >> 32) & G::kFpMask;
+  const uint32_t raw = uint32_t(k.h >> 32) & G::kFpMask;
   k.fp = raw ? raw : 1u;
-  if constexpr (G::POLICY == 0) {
-    k.i1 = uint64_t(uint32_t(k.h)) & d.mask;
-    k.i2 = k.i1 ^ (uint64_t(fp_hash(k.fp)) & d.mask);
-  } else {
-    k.i1 = fastmod32(uint32_t(k.h), d.fm_m, d.m);
-    uint64_t j = k.i1 + offset_of<G>(d, k.fp);
-    k.i2 = j >= d.m ? j - d.m : j;
-  }
+  if constexpr (G::POLICY == 0)
+    k.i1 = uint32_t(k.h) & uint32_t(d.mask);
+  else
+    k.i1 = uint32_t(fastmod32(uint32_t(k.h), d.fm_m, d.m));
+  k.i2 = 0;
+  return k;
+}
+
+template <class G>
+__device__ __forceinline__ KeyHash hash_key(const DevFilter& d, uint64_t key) {
+  KeyHash k = hash_primary<G>(d, key);
+  k.i2 = alt_index<G>(d, k.i1, k.fp);
   return k;
 }
 
@@ -313,12 +344,14 @@ __device__ __forceinline__ typename G::Word* bucket_ptr(const DevFilter& d,
 
 // TryInsert (Alg. 1): start word (tag mod b) / tpw, wrap-around scan, CAS
 // the tag into the lowest empty lane; on a lost CAS continue from the
-// returned word.
+// returned word.  `bk` is the bucket as the caller last saw it (stale values
+// are safe: the CAS validates); on TI_FULL it holds the words as last
+// observed, so the caller can keep using it without another load.
 template <class G>
-__device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag) {
+__device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
+                                 Bucket<G>& bk) {
   using W = typename G::Word;
   W* base = bucket_ptr<G>(d, j);
-  const Bucket<G> bk = load_bucket<G, false>(base);
   const int start = int((tag % G::B) / G::kTpw);
 #pragma unroll
   for (int i = 0; i < G::kWpb; ++i) {
@@ -331,11 +364,21 @@ __device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag) {
       const int lane = first_lane<G>(z);
       const W desired = cur | (W(tag) << (lane * G::F));
       const W old = atomicCAS(base + w, cur, desired);
-      if (old == cur) return TI_OK;
+      if (old == cur) {
+        set_word<G>(bk, w, desired);
+        return TI_OK;
+      }
       cur = old;
     }
+    set_word<G>(bk, w, cur);
   }
   return TI_FULL;
+}
+
+template <class G>
+__device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag) {
+  Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
+  return try_insert_loaded<G>(d, j, tag, bk);
 }
 
 // TryRemove (Alg. 3): same scan order; CAS the lowest matching lane to 0.
@@ -372,47 +415,53 @@ struct EvictCounters {
 enum : int { EV_FAIL = 0, EV_OK = 1, EV_CONTENTION = 2 };
 
 // BFS eviction heuristic (Sec. 4.6.1).  Starts with `tag` destined for the
-// full bucket `cur`.  Each round inspects b/2 consecutive slots from a random
-// start; if some candidate's alternate bucket has an empty slot, the
-// candidate is moved there and the new tag takes its slot (two steps, the
-// first undone if the second CAS finds the slot changed).  Otherwise the
-// last candidate is swapped out and the search restarts from its alternate
-// bucket.  The b/2 alternate-bucket probes of a round are independent loads
-// and are issued together.
+// full bucket `cur`, whose words the caller passes in `bk`.  Each round
+// inspects b/2 consecutive slots from a random start; if some candidate's
+// alternate bucket has an empty slot, the candidate is moved there and the
+// new tag takes its slot (two steps, the first undone if the second CAS
+// finds the slot changed).  Otherwise the last candidate is swapped out and
+// the search restarts from its alternate bucket.
+// Memory round trips per round: the b/2 alternate-bucket probes are issued
+// together; the relocation CASes into the probed words directly; after a
+// swap, the words loaded by the direct-insert attempt in the new bucket
+// serve the next round.
 template <class G>
 __device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
-                         uint32_t tag, uint32_t& ev, uint32_t& vt,
-                         uint64_t& vb, EvictCounters& ec) {
+                         uint32_t tag, Bucket<G> bk, uint32_t& ev,
+                         uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
   using W = typename G::Word;
   constexpr int H = G::B / 2;
   while (ev < d.max_ev) {
     const uint32_t start = uint32_t(rng_next(rng) & (G::B - 1));
     W* cbase = bucket_ptr<G>(d, cur);
-    Bucket<G> bk = load_bucket<G, false>(cbase);
     if (has_empty<G>(bk)) {
       // Only reachable under concurrency (a slot freed by a rollback).
-      const int r = try_insert<G>(d, cur, tag);
+      const int r = try_insert_loaded<G>(d, cur, tag, bk);
       if (r == TI_OK) return EV_OK;
-      bk = load_bucket<G, false>(cbase);
     }
     uint32_t t[H], mv[H];
     uint64_t a[H];
+    Bucket<G> ab[H];
     bool open[H];
 #pragma unroll
     for (int k = 0; k < H; ++k) {
       t[k] = get_slot<G>(bk, (start + k) & (G::B - 1));
       a[k] = alt_of<G>(d, cur, t[k], mv[k]);
+      open[k] = t[k] != 0 && a[k] != cur;
     }
 #pragma unroll
-    for (int k = 0; k < H; ++k) {
-      open[k] = false;
-      if (t[k] != 0 && a[k] != cur)
-        open[k] = has_empty<G>(load_bucket<G, false>(bucket_ptr<G>(d, a[k])));
-    }
+    for (int k = 0; k < H; ++k)
+      if (open[k]) ab[k] = load_bucket<G, false>(bucket_ptr<G>(d, a[k]));
+#pragma unroll
+    for (int k = 0; k < H; ++k) open[k] = open[k] && has_empty<G>(ab[k]);
 #pragma unroll 1
     for (int k = 0; k < H; ++k) {
       if (!open[k]) continue;
-      const int r = try_insert<G>(d, a[k], mv[k]);
+      Bucket<G> tb = ab[0];
+#pragma unroll
+      for (int q = 1; q < H; ++q)
+        if (q == k) tb = ab[q];
+      const int r = try_insert_loaded<G>(d, a[k], mv[k], tb);
       if (r != TI_OK) {
         if (r == TI_CONTENTION) ec.contention++;
         continue;
@@ -470,7 +519,8 @@ __device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
     uint32_t moved;
     cur = alt_of<G>(d, cur, evicted, moved);
     tag = moved;
-    const int r = try_insert<G>(d, cur, tag);
+    bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
+    const int r = try_insert_loaded<G>(d, cur, tag, bk);
     if (r == TI_OK) return EV_OK;
     if (r == TI_CONTENTION) {
       ec.contention++;
@@ -486,17 +536,17 @@ __device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
 
 // Greedy DFS chain (Alg. 1 phase 2): swap the tag into a random slot of cur,
 // carry the evicted tag to its alternate bucket, try a direct insert there.
+// The words loaded by that attempt serve the next swap.
 template <class G>
 __device__ int evict_dfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
-                         uint32_t tag, uint32_t& ev, uint32_t& vt,
-                         uint64_t& vb, EvictCounters& ec) {
+                         uint32_t tag, Bucket<G> bk, uint32_t& ev,
+                         uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
   using W = typename G::Word;
   while (ev < d.max_ev) {
     const uint32_t s = uint32_t(rng_next(rng) & (G::B - 1));
     const int wi = int(s / G::kTpw), lane = int(s % G::kTpw);
     W* wp = bucket_ptr<G>(d, cur) + wi;
-    W w;
-    if constexpr (G::kW32) w = ld_cg_u32(wp); else w = ld_cg_u64(wp);
+    W w = select_word<G>(bk, wi);
     bool swapped = false;
     uint32_t evicted = 0;
     for (int tries = 0; tries < kMaxCas; ++tries) {
@@ -519,7 +569,8 @@ __device__ int evict_dfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
     uint32_t moved;
     cur = alt_of<G>(d, cur, evicted, moved);
     tag = moved;
-    const int r = try_insert<G>(d, cur, tag);
+    bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
+    const int r = try_insert_loaded<G>(d, cur, tag, bk);
     if (r == TI_OK) return EV_OK;
     if (r == TI_CONTENTION) {
       ec.contention++;
@@ -549,8 +600,9 @@ __device__ int evict_key(const DevFilter& d, const KeyHash& kh, uint32_t& ev,
   const bool first = (rng_next(rng) & 1) == 0;
   const uint64_t cur = first ? kh.i1 : kh.i2;
   const uint32_t tag = first ? t1 : t2;
-  return d.eviction == 1 ? evict_dfs<G>(d, rng, cur, tag, ev, vt, vb, ec)
-                         : evict_bfs<G>(d, rng, cur, tag, ev, vt, vb, ec);
+  const Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
+  return d.eviction == 1 ? evict_dfs<G>(d, rng, cur, tag, bk, ev, vt, vb, ec)
+                         : evict_bfs<G>(d, rng, cur, tag, bk, ev, vt, vb, ec);
 }
 
 __device__ __forceinline__ void log_victim(const DevFilter& d, uint32_t tag,

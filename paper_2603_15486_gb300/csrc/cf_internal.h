@@ -1,0 +1,55 @@
+// Host-side state shared by the translation units of libcf (not part of
+// the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cf.h"
+#include "cf_kernels.cuh"
+
+namespace cfk {
+
+// Keys per staging chunk of the host-buffer calls (default).
+constexpr uint64_t kDefaultStage = 1ull << 24;
+
+struct Stage {
+  uint64_t* keys = nullptr;
+  uint8_t* flags = nullptr;
+  cudaEvent_t in_done = nullptr, comp_done = nullptr, out_done = nullptr;
+};
+
+// Per-filter call ordering: the event of the filter's last operation and the
+// stream it ran on.  A batched launch that touched the filter instead leaves
+// a borrowed event (ext_ev) of the batch; such events are never destroyed
+// (they come from a process-wide pool), so a filter may outlive the batch.
+cf_status order_on(cf_filter* f, cudaStream_t s);
+cf_status mark(cf_filter* f, cudaStream_t s);
+void mark_external(cf_filter* f, cudaStream_t s, cudaEvent_t ev);
+cudaEvent_t pooled_event();
+void set_error(const char* what, cudaError_t e);
+void set_error_text(const char* text);
+
+}  // namespace cfk
+
+struct cf_filter {
+  cf_config cfg{};
+  int device = 0;
+  char* mem = nullptr;
+  size_t mem_bytes = 0;
+  bool owns = false;
+  cfk::DevFilter d{};
+  const cfk::Ops* ops = nullptr;
+  cudaEvent_t last_ev = nullptr;
+  cudaEvent_t ext_ev = nullptr;  // borrowed from a batch (see order_on)
+  cudaStream_t last_stream = nullptr;
+  bool has_last = false;
+  uint32_t* queue = nullptr;
+  uint64_t queue_cap = 0;
+  uint64_t stage_chunk = cfk::kDefaultStage;
+  cfk::Stage stage[2];
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  bool stage_ready = false;
+};
+

@@ -19,10 +19,21 @@ namespace cfk {
 constexpr int kBlock = 256;
 
 // Keys per thread: enough independent bucket loads in flight while keeping
-// K buckets in registers.
-template <class G>
+// K buckets in registers.  CF_K_QUERY / CF_K_MUT override the default for
+// 8-byte buckets (compile-time tuning); CF_MINB_MUT is the minimum resident
+// blocks per SM requested for the mutating kernels.
+#ifndef CF_K_QUERY
+#define CF_K_QUERY 8
+#endif
+#ifndef CF_K_MUT
+#define CF_K_MUT 4
+#endif
+#ifndef CF_MINB_MUT
+#define CF_MINB_MUT 2
+#endif
+template <class G, bool MUT>
 struct Tiles {
-  static constexpr int K = G::kBucketBytes <= 8 ? 8
+  static constexpr int K = G::kBucketBytes <= 8 ? (MUT ? CF_K_MUT : CF_K_QUERY)
                            : G::kBucketBytes <= 16 ? 4
                            : G::kBucketBytes <= 32 ? 2 : 1;
 };
@@ -37,11 +48,73 @@ __device__ __forceinline__ void st_flag(uint8_t* p, uint8_t v) {
 // REMOVE: CAS the lowest lane equal to the tag to zero (TryRemove, Alg. 3).
 // Scan order per key: words from (tag mod b) / tpw with wrap-around.
 // ---------------------------------------------------------------------------
+// One-word buckets (b*f <= 64): the loaded word is the whole bucket, so a
+// key's state is just its current word.
+template <class G, int K, bool INSERT>
+__device__ __forceinline__ void cas_many_1w(const DevFilter& d,
+                                            const uint32_t (&bkt)[K],
+                                            const uint32_t (&tag)[K],
+                                            const bool (&act)[K],
+                                            int (&res)[K]) {
+  using W = typename G::Word;
+  W cur[K];
+  bool live[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    res[k] = TI_FULL;
+    live[k] = act[k];
+    cur[k] = 0;
+    if (live[k]) cur[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k])).w[0];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
+    if (live[k] && !zero_lanes<G>(cur[k] ^ pat)) live[k] = false;
+  }
+  for (int round = 0; round < kMaxCas; ++round) {
+    W old[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!live[k]) continue;
+      const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
+      const int lane = first_lane<G>(zero_lanes<G>(cur[k] ^ pat));
+      const W desired = INSERT ? (cur[k] | (W(tag[k]) << (lane * G::F)))
+                               : (cur[k] & ~(G::kLaneMask << (lane * G::F)));
+      old[k] = atomicCAS(bucket_ptr<G>(d, bkt[k]), cur[k], desired);
+    }
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!live[k]) continue;
+      if (old[k] == cur[k]) {
+        res[k] = TI_OK;
+        live[k] = false;
+        continue;
+      }
+      cur[k] = old[k];
+      const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
+      if (!zero_lanes<G>(cur[k] ^ pat)) {
+        live[k] = false;
+        continue;
+      }
+      any = true;
+    }
+    if (!any) break;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (live[k]) res[k] = TI_CONTENTION;
+}
+
 template <class G, int K, bool INSERT>
 __device__ __forceinline__ void cas_many(const DevFilter& d,
-                                         const uint64_t (&bkt)[K],
+                                         const uint32_t (&bkt)[K],
                                          const uint32_t (&tag)[K],
                                          const bool (&act)[K], int (&res)[K]) {
+  if constexpr (G::kWpb == 1) {
+    cas_many_1w<G, K, INSERT>(d, bkt, tag, act, res);
+    return;
+  }
   using W = typename G::Word;
   Bucket<G> bk[K];
   W cur[K];
@@ -122,80 +195,215 @@ __device__ __forceinline__ void cas_many(const DevFilter& d,
 }
 
 // ---------------------------------------------------------------------------
+// Per-tile bodies.  A tile is 32*K consecutive keys of one batch handled by
+// one warp (lane l owns keys base + k*32 + l).  The single-filter kernels
+// walk a batch tile by tile; the multi-filter kernel (cf_batch.cu) hands
+// each warp tiles of many filters.  Every lane of the warp must call these
+// (they use warp votes).
+// ---------------------------------------------------------------------------
+struct TileCounts {
+  uint32_t ok = 0, fail = 0, cont = 0;
+};
+
+// Appends key indices to a filter's eviction queue: one atomic per warp.
+struct QueuePush {
+  unsigned int* count;
+  uint32_t* queue;
+  __device__ __forceinline__ void operator()(bool need, uint32_t idx,
+                                             uint32_t lane) const {
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    uint32_t pos = 0;
+    if (int(lane) == leader) pos = atomicAdd(count, __popc(bal));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+    if (need) queue[pos + __popc(bal & ((1u << lane) - 1u))] = idx;
+  }
+};
+
 // Insert, phase 1 (Alg. 1 direct insertion into i1, then i2).  Keys whose
-// two buckets are both full are appended to the eviction queue (warp
-// ballot + one atomic per warp); phase 2 runs them in k_insert_evict so that
-// the few long eviction chains do not hold whole warps of finished keys.
+// two buckets are both full go to the eviction queue; phase 2 runs them
+// separately so that the few long eviction chains do not hold whole warps
+// of finished keys.
+template <class G, int K, class Push>
+__device__ __forceinline__ void tile_insert(const DevFilter& d,
+                                            const uint64_t* __restrict__ keys,
+                                            uint64_t n, uint64_t base,
+                                            uint32_t lane,
+                                            uint8_t* __restrict__ flags,
+                                            uint32_t* __restrict__ evout,
+                                            const Push& push, TileCounts& c) {
+  bool valid[K];
+  uint32_t bkt[K], tag[K];
+  int r1[K], r2[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t i = base + uint64_t(k) * 32 + lane;
+    valid[k] = i < n;
+    const KeyHash kh = hash_primary<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
+    bkt[k] = kh.i1;
+    tag[k] = kh.fp;
+  }
+  cas_many<G, K, true>(d, bkt, tag, valid, r1);
+  // Alternate buckets only for the keys whose primary bucket was full.
+  bool act[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    act[k] = valid[k] && r1[k] == TI_FULL;
+    if (act[k]) {
+      bkt[k] = alt_index<G>(d, bkt[k], tag[k]);
+      tag[k] |= G::kChoice;
+    }
+  }
+  cas_many<G, K, true>(d, bkt, tag, act, r2);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t idx = uint32_t(base + uint64_t(k) * 32 + lane);
+    const bool ok = valid[k] && (r1[k] == TI_OK || (act[k] && r2[k] == TI_OK));
+    const bool cont = valid[k] && (r1[k] == TI_CONTENTION ||
+                                   (act[k] && r2[k] == TI_CONTENTION));
+    if (ok) {
+      c.ok++;
+      if (flags) st_flag(flags + idx, 1);
+      if (evout) evout[idx] = 0;
+    } else if (cont) {
+      // bkt/tag hold the bucket and tag of the attempt that ran out.
+      c.cont++;
+      log_victim(d, tag[k], bkt[k]);
+      if (flags) st_flag(flags + idx, 2);
+      if (evout) evout[idx] = 0;
+    }
+    push(act[k] && r2[k] == TI_FULL, idx, lane);
+  }
+}
+
+// Query (Alg. 2): Find(i1) or Find(i2).  All K first-bucket loads of a
+// thread are issued together; the second bucket is hashed and loaded only
+// for the keys not found in the first (the short-circuit of Alg. 2).  Whole
+// buckets are loaded with single vector loads (up to 256 bits), so the scan
+// order of Alg. 2 does not matter: any word matching decides.
+template <class G, int K>
+__device__ __forceinline__ void tile_contains(const DevFilter& d,
+                                              const uint64_t* __restrict__ keys,
+                                              uint64_t n, uint64_t base,
+                                              uint32_t lane,
+                                              uint8_t* __restrict__ flags) {
+  bool valid[K], hit[K];
+  uint32_t fp[K], bkt[K];
+  Bucket<G> bk[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t i = base + uint64_t(k) * 32 + lane;
+    valid[k] = i < n;
+    const KeyHash kh = hash_primary<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
+    fp[k] = kh.fp;
+    bkt[k] = kh.i1;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (valid[k]) bk[k] = load_bucket<G, true>(bucket_ptr<G>(d, bkt[k]));
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    hit[k] = valid[k] && bucket_has<G>(bk[k], fp[k]);
+    if (valid[k] && !hit[k]) {
+      bkt[k] = alt_index<G>(d, bkt[k], fp[k]);
+      bk[k] = load_bucket<G, true>(bucket_ptr<G>(d, bkt[k]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (valid[k] && !hit[k]) hit[k] = bucket_has<G>(bk[k], fp[k] | G::kChoice);
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (valid[k]) st_flag(flags + base + uint64_t(k) * 32 + lane, hit[k] ? 1 : 0);
+}
+
+// Delete (Alg. 3): TryRemove(i1) or TryRemove(i2), the K keys' CASes
+// issued together.
+template <class G, int K>
+__device__ __forceinline__ void tile_remove(const DevFilter& d,
+                                            const uint64_t* __restrict__ keys,
+                                            uint64_t n, uint64_t base,
+                                            uint32_t lane,
+                                            uint8_t* __restrict__ flags,
+                                            TileCounts& c) {
+  bool valid[K];
+  uint32_t bkt[K], tag[K];
+  int r1[K], r2[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t i = base + uint64_t(k) * 32 + lane;
+    valid[k] = i < n;
+    const KeyHash kh = hash_primary<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
+    bkt[k] = kh.i1;
+    tag[k] = kh.fp;
+  }
+  cas_many<G, K, false>(d, bkt, tag, valid, r1);
+  bool act[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    act[k] = valid[k] && r1[k] == TI_FULL;
+    if (act[k]) {
+      bkt[k] = alt_index<G>(d, bkt[k], tag[k]);
+      tag[k] |= G::kChoice;
+    }
+  }
+  cas_many<G, K, false>(d, bkt, tag, act, r2);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!valid[k]) continue;
+    int r;
+    if (r1[k] == TI_OK || (act[k] && r2[k] == TI_OK)) {
+      r = 1;
+      c.ok++;
+    } else if (r1[k] == TI_CONTENTION || (act[k] && r2[k] == TI_CONTENTION)) {
+      r = 2;
+      c.cont++;
+    } else {
+      r = 0;
+      c.fail++;
+    }
+    if (flags) st_flag(flags + base + uint64_t(k) * 32 + lane, uint8_t(r));
+  }
+}
+
+// Phase 2 of the insert for one queued key: the eviction loop, its victim,
+// its flag.  Returns the flag value; adds the overwrites to *ev_total.
+template <class G>
+__device__ __forceinline__ int evict_one(const DevFilter& d, uint64_t key,
+                                         uint32_t i, uint8_t* flags,
+                                         uint32_t* evout, uint32_t& ev_total,
+                                         EvictCounters& ec) {
+  const KeyHash kh = hash_key<G>(d, key);
+  uint32_t ev = 0, vt = 0;
+  uint64_t vb = 0;
+  const int r = evict_key<G>(d, kh, ev, vt, vb, ec);
+  if (r != EV_OK) log_victim(d, vt, vb);
+  if (flags) st_flag(flags + i, uint8_t(r));
+  if (evout) evout[i] = ev;
+  ev_total += ev;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Single-filter kernels: a persistent grid walks the batch's tiles.
 // ---------------------------------------------------------------------------
 template <class G, int K>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
 k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
                 uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
                 uint32_t* __restrict__ queue) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  uint32_t n_ok = 0, n_cont = 0;
-  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K)) {
-    uint32_t idx[K];
-    bool valid[K];
-    KeyHash kh[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t i = base + uint64_t(k) * 32 + lane;
-      valid[k] = i < n;
-      idx[k] = uint32_t(i);
-      kh[k] = hash_key<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
-    }
-    uint64_t bkt[K];
-    uint32_t tag[K];
-    int r1[K], r2[K];
-    bool act[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      bkt[k] = kh[k].i1;
-      tag[k] = kh[k].fp;
-      act[k] = valid[k];
-    }
-    cas_many<G, K, true>(d, bkt, tag, act, r1);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      bkt[k] = kh[k].i2;
-      tag[k] = kh[k].fp | G::kChoice;
-      act[k] = valid[k] && r1[k] == TI_FULL;
-    }
-    cas_many<G, K, true>(d, bkt, tag, act, r2);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const bool ok = valid[k] && (r1[k] == TI_OK || (r1[k] == TI_FULL && r2[k] == TI_OK));
-      const bool cont = valid[k] && (r1[k] == TI_CONTENTION ||
-                                     (r1[k] == TI_FULL && r2[k] == TI_CONTENTION));
-      const bool need = valid[k] && r1[k] == TI_FULL && r2[k] == TI_FULL;
-      if (ok) {
-        n_ok++;
-        if (flags) st_flag(flags + idx[k], 1);
-        if (evout) evout[idx[k]] = 0;
-      } else if (cont) {
-        n_cont++;
-        log_victim(d, r1[k] == TI_CONTENTION ? kh[k].fp : (kh[k].fp | G::kChoice),
-                   r1[k] == TI_CONTENTION ? kh[k].i1 : kh[k].i2);
-        if (flags) st_flag(flags + idx[k], 2);
-        if (evout) evout[idx[k]] = 0;
-      }
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
-      if (bal) {
-        const int leader = __ffs(bal) - 1;
-        uint32_t pos = 0;
-        if (int(lane) == leader) pos = atomicAdd(&d.ctrl->queue_count, __popc(bal));
-        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-        if (need) queue[pos + __popc(bal & ((1u << lane) - 1u))] = idx[k];
-      }
-    }
-  }
-  block_add(&d.ctrl->occupancy, n_ok);
-  block_add(&d.ctrl->insert_ok, n_ok);
-  block_add(&d.ctrl->insert_fail, n_cont);
-  block_add(&d.ctrl->contention, n_cont);
+  TileCounts c;
+  const QueuePush push{&d.ctrl->queue_count, queue};
+  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K))
+    tile_insert<G, K>(d, keys, n, base, lane, flags, evout, push, c);
+  block_add(&d.ctrl->occupancy, c.ok);
+  block_add(&d.ctrl->insert_ok, c.ok);
+  block_add(&d.ctrl->insert_fail, c.cont);
+  block_add(&d.ctrl->contention, c.cont);
 }
 
 // Insert, phase 2: the eviction loop for every queued key.  The queue length
@@ -212,14 +420,7 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < qn;
        e += gridDim.x * blockDim.x) {
     const uint32_t i = queue[e];
-    const KeyHash kh = hash_key<G>(d, keys[i]);
-    uint32_t ev = 0, vt = 0;
-    uint64_t vb = 0;
-    const int r = evict_key<G>(d, kh, ev, vt, vb, ec);
-    if (r != EV_OK) log_victim(d, vt, vb);
-    if (flags) st_flag(flags + i, uint8_t(r));
-    if (evout) evout[i] = ev;
-    n_ev += ev;
+    const int r = evict_one<G>(d, keys[i], i, flags, evout, n_ev, ec);
     if (r == EV_OK) n_ok++; else n_fail++;
   }
   block_add(&d.ctrl->occupancy, n_ok);
@@ -290,13 +491,6 @@ __global__ void k_insert_serial(DevFilter d, const uint64_t* __restrict__ keys,
   atomicAdd(&d.ctrl->contention, (unsigned long long)ec.contention);
 }
 
-// ---------------------------------------------------------------------------
-// Query (Alg. 2): Find(i1) or Find(i2).  All K first-bucket loads of a
-// thread are issued together; the second buckets are loaded only for the
-// keys not found in the first (the short-circuit of Alg. 2).  Whole buckets
-// are loaded with single vector loads (up to 256 bits), so the scan order
-// of Alg. 2 does not matter: any word matching decides.
-// ---------------------------------------------------------------------------
 template <class G, int K>
 __global__ void __launch_bounds__(kBlock)
 k_contains(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
@@ -304,96 +498,24 @@ k_contains(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K)) {
-    bool valid[K], hit[K];
-    KeyHash kh[K];
-    Bucket<G> bk[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t i = base + uint64_t(k) * 32 + lane;
-      valid[k] = i < n;
-      kh[k] = hash_key<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (valid[k]) bk[k] = load_bucket<G, true>(bucket_ptr<G>(d, kh[k].i1));
-#pragma unroll
-    for (int k = 0; k < K; ++k) hit[k] = valid[k] && bucket_has<G>(bk[k], kh[k].fp);
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (valid[k] && !hit[k])
-        bk[k] = load_bucket<G, true>(bucket_ptr<G>(d, kh[k].i2));
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (valid[k] && !hit[k]) hit[k] = bucket_has<G>(bk[k], kh[k].fp | G::kChoice);
-    if (flags) {
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (valid[k]) st_flag(flags + base + uint64_t(k) * 32 + lane, hit[k] ? 1 : 0);
-    }
-  }
+  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K))
+    tile_contains<G, K>(d, keys, n, base, lane, flags);
 }
 
-// ---------------------------------------------------------------------------
-// Delete (Alg. 3): TryRemove(i1) or TryRemove(i2), K keys per thread with
-// their CASes issued together.
-// ---------------------------------------------------------------------------
 template <class G, int K>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
 k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
          uint8_t* __restrict__ flags) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  uint32_t n_ok = 0, n_fail = 0, n_cont = 0;
-  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K)) {
-    bool valid[K];
-    KeyHash kh[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t i = base + uint64_t(k) * 32 + lane;
-      valid[k] = i < n;
-      kh[k] = hash_key<G>(d, valid[k] ? ld_stream_u64(keys + i) : 0ull);
-    }
-    uint64_t bkt[K];
-    uint32_t tag[K];
-    int r1[K], r2[K];
-    bool act[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      bkt[k] = kh[k].i1;
-      tag[k] = kh[k].fp;
-      act[k] = valid[k];
-    }
-    cas_many<G, K, false>(d, bkt, tag, act, r1);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      bkt[k] = kh[k].i2;
-      tag[k] = kh[k].fp | G::kChoice;
-      act[k] = valid[k] && r1[k] == TI_FULL;
-    }
-    cas_many<G, K, false>(d, bkt, tag, act, r2);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!valid[k]) continue;
-      int r;
-      if (r1[k] == TI_OK || (r1[k] == TI_FULL && r2[k] == TI_OK)) {
-        r = 1;
-        n_ok++;
-      } else if (r1[k] == TI_CONTENTION || r2[k] == TI_CONTENTION) {
-        r = 2;
-        n_cont++;
-      } else {
-        r = 0;
-        n_fail++;
-      }
-      if (flags) st_flag(flags + base + uint64_t(k) * 32 + lane, uint8_t(r));
-    }
-  }
-  block_add(&d.ctrl->occupancy, n_ok, /*negate=*/true);
-  block_add(&d.ctrl->remove_ok, n_ok);
-  block_add(&d.ctrl->remove_fail, n_fail + n_cont);
-  block_add(&d.ctrl->contention, n_cont);
+  TileCounts c;
+  for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K))
+    tile_remove<G, K>(d, keys, n, base, lane, flags, c);
+  block_add(&d.ctrl->occupancy, c.ok, /*negate=*/true);
+  block_add(&d.ctrl->remove_ok, c.ok);
+  block_add(&d.ctrl->remove_fail, c.fail + c.cont);
+  block_add(&d.ctrl->contention, c.cont);
 }
 
 // Hash export for tests: fp, i1, i2 per key.
@@ -445,25 +567,26 @@ inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
 
 template <class G>
 struct Launch {
-  static constexpr int K = Tiles<G>::K;
+  static constexpr int KQ = Tiles<G, false>::K;
+  static constexpr int KM = Tiles<G, true>::K;
 
   static cudaError_t contains(const DevFilter& d, const uint64_t* keys,
                               uint64_t n, uint8_t* flags, cudaStream_t s) {
-    auto fn = k_contains<G, K>;
-    fn<<<persistent_grid(fn, n, kBlock * K), kBlock, 0, s>>>(d, keys, n, flags);
+    auto fn = k_contains<G, KQ>;
+    fn<<<persistent_grid(fn, n, kBlock * KQ), kBlock, 0, s>>>(d, keys, n, flags);
     return cudaGetLastError();
   }
   static cudaError_t remove(const DevFilter& d, const uint64_t* keys,
                             uint64_t n, uint8_t* flags, cudaStream_t s) {
-    auto fn = k_remove<G, K>;
-    fn<<<persistent_grid(fn, n, kBlock * K), kBlock, 0, s>>>(d, keys, n, flags);
+    auto fn = k_remove<G, KM>;
+    fn<<<persistent_grid(fn, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags);
     return cudaGetLastError();
   }
   static cudaError_t insert_chunk(const DevFilter& d, const uint64_t* keys,
                                   uint32_t n, uint8_t* flags, uint32_t* evout,
                                   uint32_t* queue, cudaStream_t s) {
-    auto f1 = k_insert_direct<G, K>;
-    f1<<<persistent_grid(f1, n, kBlock * K), kBlock, 0, s>>>(d, keys, n, flags,
+    auto f1 = k_insert_direct<G, KM>;
+    f1<<<persistent_grid(f1, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags,
                                                              evout, queue);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

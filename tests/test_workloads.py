@@ -43,3 +43,15 @@ def test_load_factor_counts():
     assert workloads.lf_count(1 << 28, 4, 0.95) == 1020054732
     assert workloads.lf_count(1 << 28, 4, 0.8) == 858993459
     assert workloads.LARGE.insert_segments()[-1] == (858993459, 1020054732)
+
+
+def test_zipf_keys_are_skewed_and_from_the_universe():
+    z = workloads.zipf_keys(200000, 50000, 1.1)
+    uni = workloads.keys(3, 50000)
+    assert np.isin(z, uni).all()
+    vals, counts = np.unique(z, return_counts=True)
+    counts = np.sort(counts)[::-1]
+    # Rank 1 is the most frequent key: P(r=1) is about 1 - 2^(-0.1) of the
+    # continuous law's mass on [1, 2), far above uniform.
+    assert counts[0] > 20 * 200000 / 50000
+    assert int((z == uni[0]).sum()) == int(counts[0])  # rank 1 = first key

@@ -20,6 +20,7 @@ from .gen import (  # noqa: F401
     low32_keys_dev,
     query_mix,
     query_mix_dev,
+    zipf_keys,
 )
 from .configs import (  # noqa: F401
     BY_NAME,

@@ -21,6 +21,7 @@
 // (Sec. 5.2) and, for the FPR experiment, positives from [0, 2^32) and
 // negatives from [2^32, 2^64) (Sec. 5.3).
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -167,6 +168,26 @@ int wl_high_dev(uint64_t* out, uint64_t n, uint64_t seed, uint64_t start,
   if (n == 0) return 0;
   k_high<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(out, n, seed, start);
   return launch_status();
+}
+
+// Zipf(s)-duplicated keys (host only): element i draws a rank r in [1, U]
+// from the continuous power-law approximation of Zipf(s) by inverse CDF,
+//   r = floor(((U^(1-s) - 1) * u + 1)^(1/(1-s))),  u uniform in [0, 1),
+// and returns the r-th key of the splitmix64 stream `key_seed` (so the
+// key universe has U distinct keys and popular keys repeat).  Host only:
+// floating-point pow may differ between host and device libraries, and the
+// stream must be the same bytes for every consumer; copy it to the device.
+void wl_zipf_host(uint64_t* out, uint64_t n, uint64_t rank_seed,
+                  uint64_t key_seed, uint64_t universe, double s) {
+  const double a = 1.0 - s;
+  const double top = pow((double)universe, a) - 1.0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const double u = (double)(splitmix64_at(rank_seed, i) >> 11) * 0x1.0p-53;
+    double r = floor(pow(top * u + 1.0, 1.0 / a));
+    if (r < 1.0) r = 1.0;
+    if (r > (double)universe) r = (double)universe;
+    out[i] = splitmix64_at(key_seed, (uint64_t)r - 1);
+  }
 }
 
 }  // extern "C"

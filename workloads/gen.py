@@ -64,6 +64,7 @@ def lib():
             L.wl_query_mix_host.argtypes = [vp, u64, vp, u64, u64, u64, u64]
             L.wl_low32_host.argtypes = [vp, u64, u32, u64]
             L.wl_high_host.argtypes = [vp, u64, u64, u64]
+            L.wl_zipf_host.argtypes = [vp, u64, u64, u64, u64, ctypes.c_double]
             for n in ("wl_splitmix64_dev", "wl_high_dev"):
                 getattr(L, n).argtypes = [vp, u64, u64, u64, vp]
                 getattr(L, n).restype = ctypes.c_int
@@ -109,6 +110,15 @@ def high_keys(seed: int, n: int, start: int = 0) -> np.ndarray:
     """Keys in [2^32, 2^64) (disjoint from every low32 key)."""
     out = np.empty(int(n), np.uint64)
     lib().wl_high_host(_p(out), out.size, seed, start)
+    return out
+
+
+def zipf_keys(n: int, universe: int, s: float = 1.1, rank_seed: int = 33,
+              key_seed: int = 3) -> np.ndarray:
+    """n Zipf(s)-duplicated keys over a universe of `universe` distinct
+    splitmix64 keys (continuous power-law inverse CDF; host only)."""
+    out = np.empty(int(n), np.uint64)
+    lib().wl_zipf_host(_p(out), out.size, rank_seed, key_seed, universe, s)
     return out
 
 
