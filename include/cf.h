@@ -201,6 +201,37 @@ cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
                                  uint64_t n, uint8_t* out_flags,
                                  uint32_t* evictions_out, void* stream);
 
+/* ---- insert without device allocation ------------------------------------
+ * The paper has no counterpart to this entry point.
+ *
+ * cf_insert keeps a work queue of 4 bytes per key in device memory that the
+ * library cudaMalloc's on a filter's first large insert (and reuses after).
+ * Some callers cannot allow a device allocation there: code whose device
+ * memory is all handed out by another allocator or a fixed-size arena,
+ * code on a path that must not stall on cudaMalloc's implicit device
+ * synchronisation, and code that must not fail with out-of-memory halfway
+ * through a batch.  cf_insert_noalloc does exactly the insert of cf_insert
+ * (same kernels, same results and flags) with its queue in a fixed array
+ * compiled into the library: a file-scope __device__ array of
+ * CF_NOALLOC_MAX_KEYS entries (4 MiB), which every GPU that loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or other device-allocating routine.  Keys and flags are still the
+ * caller's; build the filter with cf_create_at to keep the whole path free
+ * of library allocations.
+ *  - n > CF_NOALLOC_MAX_KEYS returns CF_EINVAL (split larger batches).
+ *  - The filter's device must be the current device (CF_EINVAL otherwise).
+ *    The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *  - Every call shares the one array: calls whose GPU work overlaps (on
+ *    streams not ordered with each other, on any filters) race and corrupt
+ *    each other's results.  Issue them on one stream or order the streams.
+ *  - The array keeps the previous call's entries.  None of it has to start
+ *    at zero: each entry is written before it is read, and the entry count
+ *    lives in the filter's control block. */
+#define CF_NOALLOC_MAX_KEYS (1u << 20)
+cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
+                            uint8_t* out_flags, void* stream);
+
 /* ---- measurement helpers ------------------------------------------------ */
 /* Random-gather ceiling: n_access independent loads of access_bytes (8, 16
  * or 32) at pseudo-random aligned offsets within the first power-of-two

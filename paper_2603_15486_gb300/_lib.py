@@ -57,6 +57,7 @@ SIGNATURES = {
     "cf_count_occupied": (_st, [_vp, ctypes.POINTER(_u64), _vp]),
     "cf_hash_debug": (_st, [_vp, _u64, _u32, _u64, _u32, _vp, _vp, _vp, _vp]),
     "cf_debug_insert_serial": (_st, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "cf_insert_noalloc": (_st, [_vp, _vp, _u64, _vp, _vp]),
     "cf_probe_gather": (_st, [_vp, _u64, _u64, _u32, _u32, _u64, _vp, _vp]),
     "cf_set_l2_fetch_granularity": (_st, [_u32]),
     "cf_get_l2_fetch_granularity": (_st, [ctypes.POINTER(_u32)]),
