@@ -440,12 +440,126 @@ def reference_arm(args):
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------------------
+# Many-filters mode: plain per-filter calls vs one batched launch per phase.
+# ---------------------------------------------------------------------------
+def batched_arm(args):
+    import torch
+
+    import workloads
+    from paper_2603_15486_gb300 import Batch, CuckooFilter
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    layout = workloads.multi_filter_layout()
+    total = sum(n for _, n in layout)
+    filters = [CuckooFilter(m, 16, 4, 500) for m, _ in layout]
+    # Keys: filter i uses splitmix64 stream 1000+i; its queries are its n_i
+    # keys followed by n_i negatives (the next outputs of the same stream).
+    ins = torch.empty(total, dtype=torch.int64, device=dev)
+    qry = torch.empty(2 * total, dtype=torch.int64, device=dev)
+    views = []
+    off = qoff = 0
+    for i, (m, n) in enumerate(layout):
+        workloads.keys_dev(ins[off:].data_ptr(), n, 1000 + i, 0, sh)
+        workloads.keys_dev(qry[qoff:].data_ptr(), 2 * n, 1000 + i, 0, sh)
+        views.append((ins[off:off + n], qry[qoff:qoff + 2 * n], ins[off:off + n // 2]))
+        off += n
+        qoff += 2 * n
+    f_ins = torch.empty(total, dtype=torch.uint8, device=dev)
+    f_q = torch.empty(2 * total, dtype=torch.uint8, device=dev)
+    f_d = torch.empty(sum(n // 2 for _, n in layout), dtype=torch.uint8, device=dev)
+    fl = []
+    off = qoff = doff = 0
+    for _, n in layout:
+        fl.append((f_ins[off:off + n], f_q[qoff:qoff + 2 * n], f_d[doff:doff + n // 2]))
+        off += n
+        qoff += 2 * n
+        doff += n // 2
+    stream.synchronize()
+    ops = total + 2 * total + sum(n // 2 for _, n in layout)
+
+    P_i, P_q, P_d = (Batch(len(layout), 2 * total) for _ in range(3))
+    P_i.set([(f, "insert", v[0], x[0]) for f, v, x in zip(filters, views, fl)])
+    P_q.set([(f, "contains", v[1], x[1]) for f, v, x in zip(filters, views, fl)])
+    P_d.set([(f, "remove", v[2], x[2]) for f, v, x in zip(filters, views, fl)])
+
+    def clear():
+        for f in filters:
+            f.clear(stream=stream)
+
+    def plain():
+        for f, v, x in zip(filters, views, fl):
+            f.insert(v[0], flags=x[0], stream=stream)
+        for f, v, x in zip(filters, views, fl):
+            f.contains(v[1], out=x[1], stream=stream)
+        for f, v, x in zip(filters, views, fl):
+            f.remove(v[2], out=x[2], stream=stream)
+
+    def batched(graph):
+        P_i.launch(stream=stream, graph=graph)
+        P_q.launch(stream=stream, graph=graph)
+        P_d.launch(stream=stream, graph=graph)
+
+    def timed(fn):
+        ms = []
+        for i in range(args.warmup + args.steps):
+            clear()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            stream.synchronize()
+            if i >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        check = {"insert_fail": int((f_ins != 1).sum()),
+                 "query_pos_missing": sum(int((x[1][:n] != 1).sum()) for x, (_, n) in zip(fl, layout)),
+                 "false_positives": sum(int(x[1][n:].sum()) for x, (_, n) in zip(fl, layout)),
+                 "remove_fail": int((f_d != 1).sum())}
+        return ops / med / 1e3, med, check
+
+    # Tune on realistic state: inserts on empty filters, the rest after them.
+    tune = {}
+    clear()
+    tune["insert"] = P_i.autotune(stream=stream)
+    P_i.launch(stream=stream)
+    tune["contains"] = P_q.autotune(stream=stream)
+    tune["remove"] = P_d.autotune(stream=stream)
+    stream.synchronize()
+
+    plain_mops, plain_ms, plain_chk = timed(plain)
+    b_mops, b_ms, b_chk = timed(lambda: batched(False))
+    g_mops, g_ms, g_chk = timed(lambda: batched(True))
+    return {
+        "metric": "multi-filter insert/query/delete Mops/s (one batched launch vs a loop of per-filter launches)",
+        "mode": "batched", "value": round(g_mops, 2), "unit": "Mops/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "config": {"workload": "512 filters, 2^8-2^22 buckets x 4 slots, f16, keys 10^2-10^6 "
+                               "log-uniform clipped to LF 0.95; insert, query (n pos + n neg), "
+                               "delete n/2", "filters": len(layout), "keys": total,
+                   "table_bytes": sum(m * 8 for m, _ in layout), "ops_per_step": ops},
+        "plain": {"mops": round(plain_mops, 2), "ms": round(plain_ms, 3), "checks": plain_chk},
+        "batched": {"mops": round(b_mops, 2), "ms": round(b_ms, 3), "checks": b_chk},
+        "graph": {"mops": round(g_mops, 2), "ms": round(g_ms, 3), "checks": g_chk},
+        "speedup_vs_plain": round(g_mops / plain_mops, 2),
+        "tuning": tune,
+        "gpu_launches_per_step": {"plain": sum(2 + 1 + 1 for _ in layout), "batched": 2 + 1 + 1},
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["main", "batched"], default="main",
+                    help="main: the large-filter headline; batched: the "
+                         "many-filters workload (one JSON line each)")
     ap.add_argument("--workload", default="large_2^28x4_f16_lf0.95")
     ap.add_argument("--cpu-workload", default="scale_2^22x4_f16_lf0.95")
     ap.add_argument("--ref-workload", default="ref_2^20x4_f16_lf0.95")
@@ -458,7 +572,12 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1")
-    out = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
+    if args.impl == "reference":
+        out = reference_arm(args)
+    elif args.mode == "batched":
+        out = batched_arm(args)
+    else:
+        out = gpu_arm(args)
     if out is not None:
         print(json.dumps(out), flush=True)
     try:

@@ -201,6 +201,164 @@ cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
                                  uint64_t n, uint8_t* out_flags,
                                  uint32_t* evictions_out, void* stream);
 
+/* ---- multi-filter launch --------------------------------------------------
+ * Many filters' insert / query / delete batches in ONE persistent kernel
+ * (plus one eviction kernel over the inserts' combined eviction queue):
+ * warps take 32*K-key tiles of all items from a device counter, so items of
+ * very different sizes keep every SM busy and no host loop launches per
+ * filter.  The algorithms per key are those of cf_insert / cf_contains /
+ * cf_remove (Alg. 1-3, Sec. 4.6.1), with the same results and flags.
+ *
+ * Rules for one batch (CF_EINVAL otherwise):
+ *  - all filters share fp_bits, slots_per_bucket and policy;
+ *  - a filter may appear in several items, but either only in queries or
+ *    only in inserts/removes (a query must not overlap a mutation, Sec. 4.4);
+ *  - n < 2^32 per item, sum of n <= max_keys, n_items <= max_items;
+ *  - out_flags is required for CF_OP_CONTAINS (device, n bytes).
+ * Ordering: the launch waits for each filter's previous work on other
+ * streams, and later calls on those filters wait for the batch. */
+typedef struct cf_batch cf_batch;
+enum { CF_OP_INSERT = 0, CF_OP_CONTAINS = 1, CF_OP_REMOVE = 2 };
+typedef struct {
+  cf_filter* filter;
+  const uint64_t* keys;  /* device */
+  uint64_t n;
+  uint8_t* out_flags;    /* device, may be NULL except for CF_OP_CONTAINS */
+  uint32_t op;
+  uint32_t reserved;
+} cf_batch_item;
+/* One configuration of the batched kernels (see cf_batch_autotune). */
+typedef struct {
+  uint32_t variant;          /* index in the geometry's variant list       */
+  uint32_t keys_per_thread;  /* K: keys a thread handles per tile          */
+  uint32_t block;            /* threads per block of the tile kernel       */
+  uint32_t frontier;         /* BFS candidates whose alternate buckets are
+                                probed together (1 .. b/2)                 */
+  float ms;                  /* launch time measured by the autotuner      */
+} cf_tuning;
+
+/* A reusable plan: device descriptor buffer, pinned host staging and an
+ * eviction queue of max_keys entries (8 bytes each).  Allocates. */
+cf_status cf_batch_create(uint32_t max_items, uint64_t max_keys,
+                          cf_batch** out);
+/* Waits for the plan's outstanding work and frees it.  NULL accepted. */
+cf_status cf_batch_destroy(cf_batch* b);
+/* Stage items (host work only; waits if the previous launch's upload has
+ * not run yet).  Picks the variant cached for this batch's class if the
+ * autotuner has seen one, else the pinned variant, else the default. */
+cf_status cf_batch_set(cf_batch* b, const cf_batch_item* items,
+                       uint32_t n_items);
+/* Enqueue the staged batch on `stream`: descriptor upload (H2D from the
+ * pinned staging), the tile kernel, the eviction kernel if any item
+ * inserts.  Asynchronous. */
+cf_status cf_batch_launch(cf_batch* b, void* stream);
+/* The same work as one CUDA-graph launch: captured on first use for the
+ * current variant, replayed afterwards (new items via cf_batch_set). */
+cf_status cf_batch_graph_launch(cf_batch* b, void* stream);
+/* Time every variant of the staged batch's geometry on the staged batch
+ * itself (the filters' device state is saved before and restored after
+ * each trial, so the batch's effect is not applied), keep the fastest for
+ * this plan and for later batches of the same class (geometry, ops, size
+ * class).  Synchronous; needs scratch memory of the filters' size. */
+cf_status cf_batch_autotune(cf_batch* b, void* stream, cf_tuning* chosen);
+cf_status cf_batch_set_variant(cf_batch* b, uint32_t variant);
+cf_status cf_batch_get_tuning(const cf_batch* b, cf_tuning* out);
+/* Number of variants for the staged batch's geometry (0 if none staged). */
+uint32_t cf_batch_variant_count(const cf_batch* b);
+
+/* ---- serving loop with continuous batching -------------------------------
+ * A server owns many live filters (all device-resident) and a scheduler
+ * thread.  Clients submit requests (filter, op, device keys, device flags)
+ * at any time.  The scheduler keeps up to max_inflight waves on the GPU,
+ * each wave one multi-filter launch (cf_batch) on its own stream: as soon
+ * as a wave slot frees up it takes the waiting requests of every filter
+ * that has no work in flight, so requests that arrive while others run are
+ * admitted as slots free up and their work overlaps on the device.
+ * Per filter, requests run in submission order (a filter is in at most one
+ * wave at a time; consecutive requests of the same kind may share a wave),
+ * so a query never overlaps a mutation of its filter (Sec. 4.4).
+ * New filters are admitted against an HBM budget: a filter that does not
+ * fit waits (its requests queue) until removed filters free enough.
+ * Thread safety: submit / add / remove / poll / drain may be called from
+ * any host thread. */
+typedef struct cf_server cf_server;
+typedef struct {
+  uint64_t hbm_budget_bytes;  /* sum of cf_required_bytes of live filters   */
+  uint32_t max_inflight;      /* waves on the GPU at once (streams), >= 1   */
+  uint32_t max_wave_items;    /* requests per wave                          */
+  uint64_t max_wave_keys;     /* keys per wave; also the largest request    */
+  uint32_t use_graphs;        /* replay each wave slot's launch as a graph  */
+  uint32_t watchdog_ms;       /* a wave running longer is "late": its
+                                 requests complete with CF_ETIMEOUT (their
+                                 results are still written); 0 = off        */
+} cf_server_config;
+typedef struct {
+  uint32_t filter_id;
+  uint32_t op;              /* CF_OP_INSERT / CF_OP_CONTAINS / CF_OP_REMOVE */
+  const uint64_t* keys;     /* device, valid until the request completes   */
+  uint64_t n;
+  uint8_t* out_flags;       /* device; required for CF_OP_CONTAINS          */
+  uint64_t tag;             /* returned in the completion                   */
+} cf_request;
+typedef struct {
+  uint64_t request_id;
+  uint64_t tag;
+  int32_t status;           /* CF_OK, or CF_ETIMEOUT for a late wave        */
+  uint32_t wave_size;       /* requests in the wave that ran this one       */
+  double submit_s;          /* host steady-clock seconds                    */
+  double launch_s;
+  double done_s;            /* when the scheduler saw the wave complete     */
+} cf_completion;
+typedef struct {
+  uint64_t submitted, completed, waves, late_waves;
+  uint64_t keys_completed;
+  uint64_t used_bytes;      /* HBM held by live filters                     */
+  uint32_t live_filters, pending_filters;
+} cf_server_stats_t;
+enum { CF_FILTER_PENDING = 0, CF_FILTER_LIVE = 1, CF_FILTER_CLOSING = 2,
+       CF_FILTER_CLOSED = 3 };
+
+cf_status cf_server_create(const cf_server_config* cfg, cf_server** out);
+/* Drains outstanding requests, stops the scheduler, frees every filter. */
+cf_status cf_server_destroy(cf_server* s);
+/* Register a filter; it becomes live when the budget allows (CF_ENOMEM if
+ * it can never fit).  Requests may be submitted to it at once. */
+cf_status cf_server_add_filter(cf_server* s, const cf_config* cfg,
+                               uint32_t* filter_id);
+/* Close a filter after its queued requests; frees its budget. */
+cf_status cf_server_remove_filter(cf_server* s, uint32_t filter_id);
+cf_status cf_server_filter_state(cf_server* s, uint32_t filter_id,
+                                 int32_t* state);
+/* The live filter object (for cf_stats / cf_snapshot once its requests
+ * have drained); NULL unless live. */
+cf_filter* cf_server_get_filter(cf_server* s, uint32_t filter_id);
+/* Queue one request (non-blocking).  CF_EINVAL for an unknown filter, a bad
+ * op, n > max_wave_keys, or a query without out_flags. */
+cf_status cf_server_submit(cf_server* s, const cf_request* r,
+                           uint64_t* request_id);
+/* Move up to max completions (in completion order) to `out`; returns how
+ * many were written. */
+uint32_t cf_server_poll(cf_server* s, cf_completion* out, uint32_t max);
+/* Wait until every submitted request has completed; CF_ETIMEOUT after
+ * timeout_ms (the work keeps running; the context is untouched). */
+cf_status cf_server_drain(cf_server* s, uint32_t timeout_ms);
+cf_status cf_server_stats(cf_server* s, cf_server_stats_t* out);
+/* Replay a trace through the server: request i is submitted at
+ * arrival_s[i] seconds after the call starts (busy-waiting the host
+ * clock), then everything is drained; completions are written by request
+ * index (out[i]).  The latency of request i is out[i].done_s -
+ * out[i].submit_s. */
+cf_status cf_server_run_trace(cf_server* s, const cf_request* reqs,
+                              const double* arrival_s, uint32_t n,
+                              cf_completion* out);
+/* The baseline the server is compared with: the same trace run by one
+ * host thread with one plain cf_insert / cf_contains / cf_remove call per
+ * request on one stream, each synchronised before the next starts (a
+ * request waits for every earlier one).  filters[r.filter_id] is used. */
+cf_status cf_plain_run_trace(cf_filter* const* filters, uint32_t n_filters,
+                             const cf_request* reqs, const double* arrival_s,
+                             uint32_t n, cf_completion* out, void* stream);
+
 /* ---- insert without device allocation ------------------------------------
  * The paper has no counterpart to this entry point.
  *

@@ -10,6 +10,8 @@ from . import _lib
 
 _lib.load()
 
-from .filter import CuckooFilter, hash_debug, make_config, required_bytes  # noqa: E402,F401
+from .filter import (Batch, CuckooFilter, Server, hash_debug, make_config,  # noqa: E402,F401
+                     plain_run_trace, required_bytes)
 
-__all__ = ["CuckooFilter", "hash_debug", "make_config", "required_bytes"]
+__all__ = ["Batch", "CuckooFilter", "Server", "hash_debug", "make_config",
+           "plain_run_trace", "required_bytes"]

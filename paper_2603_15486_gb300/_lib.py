@@ -27,6 +27,43 @@ class CfStats(ctypes.Structure):
         ("error_word", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32)]
 
 
+class CfBatchItem(ctypes.Structure):
+    _fields_ = [("filter", ctypes.c_void_p), ("keys", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("out_flags", ctypes.c_void_p),
+                ("op", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class CfTuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("keys_per_thread", ctypes.c_uint32),
+                ("block", ctypes.c_uint32), ("frontier", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
+
+
+class CfServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_wave_items", ctypes.c_uint32), ("max_wave_keys", ctypes.c_uint64),
+                ("use_graphs", ctypes.c_uint32), ("watchdog_ms", ctypes.c_uint32)]
+
+
+class CfRequest(ctypes.Structure):
+    _fields_ = [("filter_id", ctypes.c_uint32), ("op", ctypes.c_uint32),
+                ("keys", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("out_flags", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class CfCompletion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("tag", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("wave_size", ctypes.c_uint32),
+                ("submit_s", ctypes.c_double), ("launch_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class CfServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "waves", "late_waves", "keys_completed", "used_bytes")] + [
+        ("live_filters", ctypes.c_uint32), ("pending_filters", ctypes.c_uint32)]
+
+
 # Every symbol include/cf.h declares, with (restype, argtypes).
 _vp, _u64, _u32, _int = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
 _st = ctypes.c_int
@@ -58,6 +95,30 @@ SIGNATURES = {
     "cf_hash_debug": (_st, [_vp, _u64, _u32, _u64, _u32, _vp, _vp, _vp, _vp]),
     "cf_debug_insert_serial": (_st, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "cf_insert_noalloc": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_server_create": (_st, [ctypes.POINTER(CfServerConfig), ctypes.POINTER(_vp)]),
+    "cf_server_destroy": (_st, [_vp]),
+    "cf_server_add_filter": (_st, [_vp, _pcfg, ctypes.POINTER(_u32)]),
+    "cf_server_remove_filter": (_st, [_vp, _u32]),
+    "cf_server_filter_state": (_st, [_vp, _u32, ctypes.POINTER(ctypes.c_int32)]),
+    "cf_server_get_filter": (_vp, [_vp, _u32]),
+    "cf_server_submit": (_st, [_vp, ctypes.POINTER(CfRequest), ctypes.POINTER(_u64)]),
+    "cf_server_poll": (_u32, [_vp, ctypes.POINTER(CfCompletion), _u32]),
+    "cf_server_drain": (_st, [_vp, _u32]),
+    "cf_server_stats": (_st, [_vp, ctypes.POINTER(CfServerStats)]),
+    "cf_server_run_trace": (_st, [_vp, ctypes.POINTER(CfRequest), ctypes.POINTER(ctypes.c_double),
+                                  _u32, ctypes.POINTER(CfCompletion)]),
+    "cf_plain_run_trace": (_st, [ctypes.POINTER(_vp), _u32, ctypes.POINTER(CfRequest),
+                                 ctypes.POINTER(ctypes.c_double), _u32,
+                                 ctypes.POINTER(CfCompletion), _vp]),
+    "cf_batch_create": (_st, [_u32, _u64, ctypes.POINTER(_vp)]),
+    "cf_batch_destroy": (_st, [_vp]),
+    "cf_batch_set": (_st, [_vp, ctypes.POINTER(CfBatchItem), _u32]),
+    "cf_batch_launch": (_st, [_vp, _vp]),
+    "cf_batch_graph_launch": (_st, [_vp, _vp]),
+    "cf_batch_autotune": (_st, [_vp, _vp, ctypes.POINTER(CfTuning)]),
+    "cf_batch_set_variant": (_st, [_vp, _u32]),
+    "cf_batch_get_tuning": (_st, [_vp, ctypes.POINTER(CfTuning)]),
+    "cf_batch_variant_count": (_u32, [_vp]),
     "cf_probe_gather": (_st, [_vp, _u64, _u64, _u32, _u32, _u64, _vp, _vp]),
     "cf_set_l2_fetch_granularity": (_st, [_u32]),
     "cf_get_l2_fetch_granularity": (_st, [ctypes.POINTER(_u32)]),

@@ -425,12 +425,13 @@ enum : int { EV_FAIL = 0, EV_OK = 1, EV_CONTENTION = 2 };
 // together; the relocation CASes into the probed words directly; after a
 // swap, the words loaded by the direct-insert attempt in the new bucket
 // serve the next round.
-template <class G>
+template <class G, int FW = G::B / 2>
 __device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
                          uint32_t tag, Bucket<G> bk, uint32_t& ev,
                          uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
   using W = typename G::Word;
   constexpr int H = G::B / 2;
+  static_assert(FW >= 1 && H % FW == 0, "frontier width divides b/2");
   while (ev < d.max_ev) {
     const uint32_t start = uint32_t(rng_next(rng) & (G::B - 1));
     W* cbase = bucket_ptr<G>(d, cur);
@@ -441,57 +442,65 @@ __device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
     }
     uint32_t t[H], mv[H];
     uint64_t a[H];
-    Bucket<G> ab[H];
-    bool open[H];
+    bool cand[H];
 #pragma unroll
     for (int k = 0; k < H; ++k) {
       t[k] = get_slot<G>(bk, (start + k) & (G::B - 1));
       a[k] = alt_of<G>(d, cur, t[k], mv[k]);
-      open[k] = t[k] != 0 && a[k] != cur;
+      cand[k] = t[k] != 0 && a[k] != cur;
     }
+    // The frontier: FW alternate buckets probed together per group, groups
+    // in candidate order; the first candidate (in order) whose alternate
+    // bucket has room is relocated, whatever FW is.
 #pragma unroll
-    for (int k = 0; k < H; ++k)
-      if (open[k]) ab[k] = load_bucket<G, false>(bucket_ptr<G>(d, a[k]));
+    for (int g = 0; g < H; g += FW) {
+      Bucket<G> ab[FW];
+      bool open[FW];
 #pragma unroll
-    for (int k = 0; k < H; ++k) open[k] = open[k] && has_empty<G>(ab[k]);
+      for (int q = 0; q < FW; ++q)
+        if (cand[g + q]) ab[q] = load_bucket<G, false>(bucket_ptr<G>(d, a[g + q]));
+#pragma unroll
+      for (int q = 0; q < FW; ++q) open[q] = cand[g + q] && has_empty<G>(ab[q]);
 #pragma unroll 1
-    for (int k = 0; k < H; ++k) {
-      if (!open[k]) continue;
-      Bucket<G> tb = ab[0];
+      for (int q = 0; q < FW; ++q) {
+        if (!open[q]) continue;
+        const int k = g + q;
+        Bucket<G> tb = ab[0];
 #pragma unroll
-      for (int q = 1; q < H; ++q)
-        if (q == k) tb = ab[q];
-      const int r = try_insert_loaded<G>(d, a[k], mv[k], tb);
-      if (r != TI_OK) {
-        if (r == TI_CONTENTION) ec.contention++;
-        continue;
-      }
-      const uint32_t c = (start + k) & (G::B - 1);
-      const int wi = int(c / G::kTpw), lane = int(c % G::kTpw);
-      W w = select_word<G>(bk, wi);
-      bool placed = false;
-      for (int tries = 0; tries < kMaxCas; ++tries) {
-        if (get_lane<G>(w, lane) != t[k]) break;  // the slot changed
-        const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, tag));
-        if (old == w) {
-          placed = true;
-          break;
+        for (int z = 1; z < FW; ++z)
+          if (z == q) tb = ab[z];
+        const int r = try_insert_loaded<G>(d, a[k], mv[k], tb);
+        if (r != TI_OK) {
+          if (r == TI_CONTENTION) ec.contention++;
+          continue;
         }
-        w = old;
+        const uint32_t c = (start + k) & (G::B - 1);
+        const int wi = int(c / G::kTpw), lane = int(c % G::kTpw);
+        W w = select_word<G>(bk, wi);
+        bool placed = false;
+        for (int tries = 0; tries < kMaxCas; ++tries) {
+          if (get_lane<G>(w, lane) != t[k]) break;  // the slot changed
+          const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, tag));
+          if (old == w) {
+            placed = true;
+            break;
+          }
+          w = old;
+        }
+        if (placed) {
+          ev++;
+          return EV_OK;
+        }
+        // Undo step 1: remove one copy of the candidate from its alternate
+        // bucket, or from the bucket it may have been moved back to.
+        ec.rollbacks++;
+        if (try_remove<G>(d, a[k], mv[k]) != TI_OK) {
+          uint32_t back;
+          const uint64_t aa = alt_of<G>(d, a[k], mv[k], back);
+          if (try_remove<G>(d, aa, back) != TI_OK) ec.rollback_lost++;
+        }
+        bk = load_bucket<G, false>(cbase);
       }
-      if (placed) {
-        ev++;
-        return EV_OK;
-      }
-      // Undo step 1: remove one copy of the candidate from its alternate
-      // bucket, or from the bucket it may have been moved back to.
-      ec.rollbacks++;
-      if (try_remove<G>(d, a[k], mv[k]) != TI_OK) {
-        uint32_t back;
-        const uint64_t aa = alt_of<G>(d, a[k], mv[k], back);
-        if (try_remove<G>(d, aa, back) != TI_OK) ec.rollback_lost++;
-      }
-      bk = load_bucket<G, false>(cbase);
     }
     // No shallow path: swap the last candidate out.
     const uint32_t c = (start + H - 1) & (G::B - 1);
@@ -586,7 +595,7 @@ __device__ int evict_dfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
 
 // Phase 2 of Alg. 1 for one key whose direct insertion failed: pick i1 or
 // i2 with the key's first random draw, then run the eviction loop.
-template <class G>
+template <class G, int FW = G::B / 2>
 __device__ int evict_key(const DevFilter& d, const KeyHash& kh, uint32_t& ev,
                          uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
   const uint32_t t1 = kh.fp, t2 = kh.fp | G::kChoice;
@@ -602,7 +611,7 @@ __device__ int evict_key(const DevFilter& d, const KeyHash& kh, uint32_t& ev,
   const uint32_t tag = first ? t1 : t2;
   const Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
   return d.eviction == 1 ? evict_dfs<G>(d, rng, cur, tag, bk, ev, vt, vb, ec)
-                         : evict_bfs<G>(d, rng, cur, tag, bk, ev, vt, vb, ec);
+                         : evict_bfs<G, FW>(d, rng, cur, tag, bk, ev, vt, vb, ec);
 }
 
 __device__ __forceinline__ void log_victim(const DevFilter& d, uint32_t tag,

@@ -369,7 +369,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
 
 // Phase 2 of the insert for one queued key: the eviction loop, its victim,
 // its flag.  Returns the flag value; adds the overwrites to *ev_total.
-template <class G>
+template <class G, int FW = G::B / 2>
 __device__ __forceinline__ int evict_one(const DevFilter& d, uint64_t key,
                                          uint32_t i, uint8_t* flags,
                                          uint32_t* evout, uint32_t& ev_total,
@@ -377,7 +377,7 @@ __device__ __forceinline__ int evict_one(const DevFilter& d, uint64_t key,
   const KeyHash kh = hash_key<G>(d, key);
   uint32_t ev = 0, vt = 0;
   uint64_t vb = 0;
-  const int r = evict_key<G>(d, kh, ev, vt, vb, ec);
+  const int r = evict_key<G, FW>(d, kh, ev, vt, vb, ec);
   if (r != EV_OK) log_victim(d, vt, vb);
   if (flags) st_flag(flags + i, uint8_t(r));
   if (evout) evout[i] = ev;

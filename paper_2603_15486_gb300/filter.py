@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CfConfig, CfStats, check
+from ._lib import (CfBatchItem, CfCompletion, CfConfig, CfRequest, CfServerConfig,
+                   CfServerStats, CfStats, CfTuning, check)
 
 POLICIES = {"xor": 0, "offset": 1}
 EVICTIONS = {"bfs": 0, "dfs": 1}
@@ -273,3 +274,198 @@ def hash_debug(keys: torch.Tensor, fp_bits: int, num_buckets: int, policy: str =
                           fp.data_ptr(), i1.data_ptr(), i2.data_ptr(),
                           _stream_handle(stream)), "cf_hash_debug")
     return fp, i1, i2
+
+
+OPS = {"insert": 0, "contains": 1, "remove": 2}
+
+
+class Batch:
+    """A multi-filter launch plan (cf_batch_*): many filters' insert /
+    query / delete batches in one persistent kernel (+ one eviction
+    kernel), optionally as a replayed CUDA graph, with an autotuner."""
+
+    def __init__(self, max_items: int, max_keys: int):
+        self._L = _lib.load()
+        h = ctypes.c_void_p()
+        check(self._L.cf_batch_create(int(max_items), int(max_keys), ctypes.byref(h)),
+              "cf_batch_create")
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.cf_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, items):
+        """items: iterable of (CuckooFilter, op, keys, flags) with op in
+        {"insert", "contains", "remove"}; keys/flags CUDA tensors (flags may
+        be None except for "contains")."""
+        items = list(items)
+        arr = (CfBatchItem * max(1, len(items)))()
+        keep = []
+        for i, (filt, op, keys, flags) in enumerate(items):
+            keys = _dev_keys(keys)
+            arr[i].filter = filt.handle
+            arr[i].keys = keys.data_ptr()
+            arr[i].n = keys.numel()
+            arr[i].out_flags = flags.data_ptr() if flags is not None else None
+            arr[i].op = OPS[op]
+            keep += [filt, keys, flags]
+        check(self._L.cf_batch_set(self._h, arr, len(items)), "cf_batch_set")
+        self._keep = keep
+
+    def launch(self, stream=None, graph: bool = False):
+        fn = self._L.cf_batch_graph_launch if graph else self._L.cf_batch_launch
+        check(fn(self._h, _stream_handle(stream)), "cf_batch_launch")
+
+    def autotune(self, stream=None) -> dict:
+        t = CfTuning()
+        check(self._L.cf_batch_autotune(self._h, _stream_handle(stream), ctypes.byref(t)),
+              "cf_batch_autotune")
+        return {n: getattr(t, n) for n, _ in CfTuning._fields_}
+
+    def set_variant(self, v: int):
+        check(self._L.cf_batch_set_variant(self._h, int(v)), "cf_batch_set_variant")
+
+    def tuning(self) -> dict:
+        t = CfTuning()
+        check(self._L.cf_batch_get_tuning(self._h, ctypes.byref(t)), "cf_batch_get_tuning")
+        return {n: getattr(t, n) for n, _ in CfTuning._fields_}
+
+    def variant_count(self) -> int:
+        return int(self._L.cf_batch_variant_count(self._h))
+
+
+FILTER_STATES = {0: "pending", 1: "live", 2: "closing", 3: "closed"}
+
+
+def _completions_to_dict(arr, n):
+    out = np.empty(n, dtype=[("request_id", "u8"), ("tag", "u8"), ("status", "i4"),
+                             ("wave_size", "u4"), ("submit_s", "f8"), ("launch_s", "f8"),
+                             ("done_s", "f8")])
+    for i in range(n):
+        c = arr[i]
+        out[i] = (c.request_id, c.tag, c.status, c.wave_size, c.submit_s, c.launch_s, c.done_s)
+    return out
+
+
+def _requests(reqs):
+    """reqs: list of (filter_id, op, keys_tensor, flags_tensor_or_None, tag)."""
+    arr = (CfRequest * max(1, len(reqs)))()
+    keep = []
+    for i, (fid, op, keys, flags, tag) in enumerate(reqs):
+        keys = _dev_keys(keys)
+        arr[i] = CfRequest(int(fid), OPS[op], keys.data_ptr(), keys.numel(),
+                           flags.data_ptr() if flags is not None else None, int(tag))
+        keep += [keys, flags]
+    return arr, keep
+
+
+class Server:
+    """Serving loop with continuous batching (cf_server_*): filters live on
+    the device, requests are batched into waves of multi-filter launches,
+    several waves in flight, filters admitted against an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4,
+                 max_wave_items: int = 256, max_wave_keys: int = 1 << 22,
+                 use_graphs: bool = True, watchdog_ms: int = 0):
+        self._L = _lib.load()
+        cfg = CfServerConfig(int(hbm_budget_bytes), int(max_inflight), int(max_wave_items),
+                             int(max_wave_keys), int(bool(use_graphs)), int(watchdog_ms))
+        h = ctypes.c_void_p()
+        check(self._L.cf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cf_server_create")
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.cf_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_filter(self, num_buckets: int, fp_bits: int = 16, slots_per_bucket: int = 4,
+                   max_evictions: int = 500, policy: str = "xor", eviction: str = "bfs") -> int:
+        cfg = make_config(num_buckets, fp_bits, slots_per_bucket, max_evictions, policy, eviction)
+        fid = ctypes.c_uint32()
+        check(self._L.cf_server_add_filter(self._h, ctypes.byref(cfg), ctypes.byref(fid)),
+              "cf_server_add_filter")
+        return fid.value
+
+    def remove_filter(self, fid: int):
+        check(self._L.cf_server_remove_filter(self._h, int(fid)), "cf_server_remove_filter")
+
+    def filter_state(self, fid: int) -> str:
+        st = ctypes.c_int32()
+        check(self._L.cf_server_filter_state(self._h, int(fid), ctypes.byref(st)),
+              "cf_server_filter_state")
+        return FILTER_STATES[st.value]
+
+    def filter_handle(self, fid: int) -> Optional[int]:
+        return self._L.cf_server_get_filter(self._h, int(fid))
+
+    def submit(self, fid: int, op: str, keys: torch.Tensor, flags=None, tag: int = 0) -> int:
+        keys = _dev_keys(keys)
+        r = CfRequest(int(fid), OPS[op], keys.data_ptr(), keys.numel(),
+                      flags.data_ptr() if flags is not None else None, int(tag))
+        rid = ctypes.c_uint64()
+        check(self._L.cf_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)),
+              "cf_server_submit")
+        self._keep[rid.value] = (keys, flags)
+        return rid.value
+
+    def poll(self, max_n: int = 4096):
+        arr = (CfCompletion * max_n)()
+        n = self._L.cf_server_poll(self._h, arr, max_n)
+        out = _completions_to_dict(arr, n)
+        for rid in out["request_id"]:
+            self._keep.pop(int(rid), None)
+        return out
+
+    def drain(self, timeout_ms: int = 600000) -> int:
+        """0 when everything submitted has completed, else the status
+        (4 = CF_ETIMEOUT)."""
+        return int(self._L.cf_server_drain(self._h, int(timeout_ms)))
+
+    def stats(self) -> dict:
+        st = CfServerStats()
+        check(self._L.cf_server_stats(self._h, ctypes.byref(st)), "cf_server_stats")
+        return {n: int(getattr(st, n)) for n, _ in CfServerStats._fields_}
+
+    def run_trace(self, reqs, arrival_s):
+        """Replay (filter_id, op, keys, flags, tag) requests at the given
+        arrival times (seconds from the start); returns the completions by
+        request index."""
+        arr, keep = _requests(reqs)
+        n = len(reqs)
+        arrivals = (ctypes.c_double * max(1, n))(*[float(a) for a in arrival_s])
+        out = (CfCompletion * max(1, n))()
+        check(self._L.cf_server_run_trace(self._h, arr, arrivals, n, out), "cf_server_run_trace")
+        return _completions_to_dict(out, n)
+
+
+def plain_run_trace(filters, reqs, arrival_s, stream=None):
+    """The baseline: each request alone, in arrival order, one synchronised
+    cf_insert / cf_contains / cf_remove at a time.  filters[i] serves
+    filter_id i."""
+    L = _lib.load()
+    arr, keep = _requests(reqs)
+    n = len(reqs)
+    fl = (ctypes.c_void_p * max(1, len(filters)))(*[f.handle if f is not None else None
+                                                    for f in filters])
+    arrivals = (ctypes.c_double * max(1, n))(*[float(a) for a in arrival_s])
+    out = (CfCompletion * max(1, n))()
+    check(L.cf_plain_run_trace(fl, len(filters), arr, arrivals, n, out,
+                               _stream_handle(stream)), "cf_plain_run_trace")
+    return _completions_to_dict(out, n)

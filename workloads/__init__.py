@@ -31,4 +31,5 @@ from .configs import (  # noqa: F401
     SINGLE,
     Workload,
     lf_count,
+    multi_filter_layout,
 )

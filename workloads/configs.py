@@ -81,3 +81,23 @@ REF_STEP = Workload(name="ref_2^20x4_f16_lf0.95", m=1 << 20, f=16, b=4,
                     n_queries=1 << 22, query_pos_seed=12, n_deletes=1 << 20)
 
 BY_NAME = {w.name: w for w in (SINGLE, LARGE, MEDIUM, SCALE, REF_STEP)}
+
+
+def multi_filter_layout(n_filters: int = 512, e_lo: int = 8, e_hi: int = 22,
+                        u_lo: float = 2.0, u_hi: float = 6.0, b: int = 4,
+                        alpha: float = 0.95, seed: int = 4):
+    """The many-filters workload: filter i has m_i = 2^e_i buckets with e_i
+    uniform in [e_lo, e_hi] and a key batch of round(10^u_i) keys with u_i
+    uniform in [u_lo, u_hi], clipped to floor(alpha * m_i * b).  Draws come
+    from splitmix64 streams `seed` (sizes) and `seed + 40` (batch sizes)."""
+    from .gen import keys as _stream
+    r1 = _stream(seed, n_filters)
+    r2 = _stream(seed + 40, n_filters)
+    out = []
+    for i in range(n_filters):
+        e = e_lo + int(r1[i] % (e_hi - e_lo + 1))
+        u = u_lo + (u_hi - u_lo) * float(int(r2[i]) >> 11) / float(1 << 53)
+        m = 1 << e
+        n = min(int(round(10 ** u)), lf_count(m, b, alpha))
+        out.append((m, n))
+    return out
