@@ -551,15 +551,110 @@ def batched_arm(args):
     }
 
 
+# ---------------------------------------------------------------------------
+# Serving mode: continuous batching vs one plain call per request.
+# ---------------------------------------------------------------------------
+def _lat_stats(c, n_keys):
+    import numpy as np
+    lat = (c["done_s"] - c["submit_s"]) * 1e3
+    span = float(c["done_s"].max() - c["submit_s"].min())
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3),
+            "mops": round(n_keys / span / 1e6, 1),
+            "req_per_s": round(len(c) / span, 1),
+            "timeouts": int((c["status"] == 4).sum()),
+            "errors": int(((c["status"] != 0) & (c["status"] != 4)).sum())}
+
+
+def serve_arm(args):
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import workloads
+    from workloads.serve import materialize
+    from paper_2603_15486_gb300 import CuckooFilter, Server, _lib, plain_run_trace
+
+    torch.cuda.set_device(0)
+    L = _lib.load()
+    stream = torch.cuda.Stream()
+    sizes, plan = workloads.serve_trace(args.serve_requests)
+    budget = 64 << 30
+    srv = Server(budget, max_inflight=4, max_wave_items=512, max_wave_keys=1 << 22,
+                 use_graphs=True)
+    fids = [srv.add_filter(m, 16, 4, 500) for m in sizes]
+    plain = [CuckooFilter(m, 16, 4, 500) for m in sizes]
+    reqs, keep = materialize(sizes, plan, stream)
+    n_keys = sum(p[2] for p in plan)
+    sreqs = [(fids[f], op, k, fl, i) for i, (f, op, k, fl) in enumerate(reqs)]
+    preqs = [(f, op, k, fl, i) for i, (f, op, k, fl) in enumerate(reqs)]
+    assert srv.drain(600000) == 0
+    while srv.stats()["live_filters"] < len(fids):
+        time.sleep(0.01)
+
+    def reset():
+        assert srv.drain(600000) == 0
+        for fid in fids:
+            h = srv.filter_handle(fid)
+            assert h, "server filter not live"
+            L.cf_clear(h, None)
+        for f in plain:
+            f.clear()
+        torch.cuda.synchronize()
+
+    R = len(reqs)
+    reset()
+    c = srv.run_trace(sreqs, [0.0] * R)
+    sat_served = _lat_stats(c, n_keys)
+    reset()
+    p = plain_run_trace(plain, preqs, [0.0] * R, stream=stream)
+    sat_plain = _lat_stats(p, n_keys)
+    cap = sat_served["req_per_s"]
+    loads = {}
+    rng = np.random.default_rng(5)
+    # Loads relative to the served capacity, plus one inside the plain
+    # baseline's own capacity (where its queue does not grow without bound).
+    points = [(f"{int(f * 100)}%", f * cap) for f in (0.5, 0.8, 0.95)]
+    points.append(("80%_of_plain_capacity", 0.8 * sat_plain["req_per_s"]))
+    for name, lam in points:
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=R))
+        arrivals -= arrivals[0]
+        reset()
+        c = srv.run_trace(sreqs, arrivals)
+        reset()
+        p = plain_run_trace(plain, preqs, arrivals, stream=stream)
+        loads[name] = {"rate_req_s": round(lam, 1),
+                                        "served": _lat_stats(c, n_keys),
+                                        "plain": _lat_stats(p, n_keys)}
+    st = srv.stats()
+    srv.close()
+    return {"metric": "served p50/p99 latency and Mops/s vs plain per-request launches",
+            "mode": "serve", "value": sat_served["mops"], "unit": "Mops/s",
+            "n_gpus": 1, "higher_is_better": True,
+            "config": {"workload": f"{R} requests over {len(sizes)} filters "
+                                   "(2^16-2^26 buckets x 4, f16), mix 1 insert : 8 query : "
+                                   "1 delete, n = 2^(20u); Poisson arrivals at 50/80/95% "
+                                   "of the served capacity", "requests": R, "keys": n_keys,
+                       "hbm_budget_bytes": budget, "max_inflight_waves": 4,
+                       "max_wave_keys": 1 << 22, "graphs": True},
+            "saturated": {"served": sat_served, "plain": sat_plain,
+                          "speedup": round(sat_served["mops"] / sat_plain["mops"], 2)},
+            "poisson": loads,
+            "server": {"waves": st["waves"], "mean_wave_requests": round(st["completed"] / max(1, st["waves"]), 2)}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["main", "batched"], default="main",
-                    help="main: the large-filter headline; batched: the "
-                         "many-filters workload (one JSON line each)")
+    ap.add_argument("--mode", choices=["main", "batched", "serve"], default="main",
+                    help="main: the large-filter headline; batched / serve: the "
+                         "many-filters and serving workloads (one JSON line each)")
+    ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--workload", default="large_2^28x4_f16_lf0.95")
     ap.add_argument("--cpu-workload", default="scale_2^22x4_f16_lf0.95")
     ap.add_argument("--ref-workload", default="ref_2^20x4_f16_lf0.95")
@@ -576,6 +671,8 @@ def main(argv=None):
         out = reference_arm(args)
     elif args.mode == "batched":
         out = batched_arm(args)
+    elif args.mode == "serve":
+        out = serve_arm(args)
     else:
         out = gpu_arm(args)
     if out is not None:

@@ -288,7 +288,8 @@ typedef struct {
   uint32_t max_wave_items;    /* requests per wave                          */
   uint64_t max_wave_keys;     /* keys per wave; also the largest request    */
   uint32_t use_graphs;        /* replay each wave slot's launch as a graph  */
-  uint32_t watchdog_ms;       /* a wave running longer is "late": its
+  uint32_t watchdog_us;       /* a wave running longer (launch to observed
+                                 completion, microseconds) is "late": its
                                  requests complete with CF_ETIMEOUT (their
                                  results are still written); 0 = off        */
 } cf_server_config;

@@ -42,7 +42,7 @@ class CfTuning(ctypes.Structure):
 class CfServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("max_wave_items", ctypes.c_uint32), ("max_wave_keys", ctypes.c_uint64),
-                ("use_graphs", ctypes.c_uint32), ("watchdog_ms", ctypes.c_uint32)]
+                ("use_graphs", ctypes.c_uint32), ("watchdog_us", ctypes.c_uint32)]
 
 
 class CfRequest(ctypes.Structure):

@@ -115,8 +115,8 @@ bool retire_waves(cf_server* s) {
     const cudaError_t q = cudaEventQuery(w.done);
     if (q == cudaErrorNotReady) continue;
     const double t = now_s();
-    const bool late = s->cfg.watchdog_ms &&
-                      (t - w.launch_s) * 1e3 > double(s->cfg.watchdog_ms);
+    const bool late = s->cfg.watchdog_us &&
+                      (t - w.launch_s) * 1e6 > double(s->cfg.watchdog_us);
     if (late) s->late++;
     const int32_t st = q != cudaSuccess ? CF_ECUDA : (late ? CF_ETIMEOUT : CF_OK);
     for (Req* r : w.reqs) complete(s, r, t, st);

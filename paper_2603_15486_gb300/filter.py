@@ -375,10 +375,10 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4,
                  max_wave_items: int = 256, max_wave_keys: int = 1 << 22,
-                 use_graphs: bool = True, watchdog_ms: int = 0):
+                 use_graphs: bool = True, watchdog_us: int = 0):
         self._L = _lib.load()
         cfg = CfServerConfig(int(hbm_budget_bytes), int(max_inflight), int(max_wave_items),
-                             int(max_wave_keys), int(bool(use_graphs)), int(watchdog_ms))
+                             int(max_wave_keys), int(bool(use_graphs)), int(watchdog_us))
         h = ctypes.c_void_p()
         check(self._L.cf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cf_server_create")
         self._h = h

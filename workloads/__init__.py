@@ -32,4 +32,5 @@ from .configs import (  # noqa: F401
     Workload,
     lf_count,
     multi_filter_layout,
+    serve_trace,
 )

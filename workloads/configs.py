@@ -101,3 +101,60 @@ def multi_filter_layout(n_filters: int = 512, e_lo: int = 8, e_hi: int = 22,
         n = min(int(round(10 ** u)), lf_count(m, b, alpha))
         out.append((m, n))
     return out
+
+
+def serve_trace(n_requests: int, n_filters: int = 64, e_lo: int = 16, e_hi: int = 26,
+                max_log2: float = 20.0, mix=(1, 8, 1), b: int = 4, fill: float = 0.9,
+                seed: int = 5):
+    """The serving workload's request sequence (host-side plan, no keys).
+
+    Filter f has 2^e_f buckets, e_f uniform in [e_lo, e_hi]; its keys are
+    splitmix64 stream 10000+f (inserted in order) and its query negatives
+    stream 20000+f.  Request r picks a filter uniformly, an op with weights
+    `mix` (insert : query : delete) and n = round(2^(max_log2 * u)), u
+    uniform in [0, 1).  Inserts take the filter's next keys (never beyond
+    `fill` of its capacity), deletes its oldest live keys, queries n/2 live
+    keys (the oldest ones) then negatives; an insert or delete with nothing
+    to do becomes a query.  Returns (bucket counts, requests) where each
+    request is (filter, op, n, pos_start, pos_n, neg_start, neg_n): keys
+    [pos_start, pos_start+pos_n) of the filter's key stream followed by
+    negatives [neg_start, neg_start+neg_n)."""
+    from .gen import keys as _stream
+    rf = _stream(seed, n_filters)
+    sizes = [1 << (e_lo + int(rf[i] % (e_hi - e_lo + 1))) for i in range(n_filters)]
+    caps = [lf_count(m, b, fill) for m in sizes]
+    ins = [0] * n_filters
+    dele = [0] * n_filters
+    neg = [0] * n_filters
+    r1 = _stream(seed + 1, n_requests)
+    r2 = _stream(seed + 2, n_requests)
+    r3 = _stream(seed + 3, n_requests)
+    tot = sum(mix)
+    reqs = []
+    for r in range(n_requests):
+        f = int(r1[r] % n_filters)
+        w = int(r2[r] % tot)
+        op = "insert" if w < mix[0] else ("contains" if w < mix[0] + mix[1] else "remove")
+        u = float(int(r3[r]) >> 11) / float(1 << 53)
+        n = max(1, int(round(2.0 ** (max_log2 * u))))
+        if op == "insert":
+            n = min(n, caps[f] - ins[f])
+            if n <= 0:
+                op, n = "contains", max(1, int(round(2.0 ** (max_log2 * u))))
+            else:
+                reqs.append((f, op, n, ins[f], n, 0, 0))
+                ins[f] += n
+                continue
+        if op == "remove":
+            n = min(n, ins[f] - dele[f])
+            if n <= 0:
+                op, n = "contains", max(1, int(round(2.0 ** (max_log2 * u))))
+            else:
+                reqs.append((f, op, n, dele[f], n, 0, 0))
+                dele[f] += n
+                continue
+        pos_n = min(n // 2, ins[f] - dele[f])
+        neg_n = n - pos_n
+        reqs.append((f, "contains", n, dele[f], pos_n, neg[f], neg_n))
+        neg[f] += neg_n
+    return sizes, reqs
