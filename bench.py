@@ -160,7 +160,10 @@ def oracle_run(W, repeat: int = 1):
         res = (t3 - t0, W.ops_per_step(),
                {"insert": {"ops": W.n_insert, "s": t1 - t0,
                            "bucket_reads": s_ins["ins_bucket_reads"],
-                           "bucket_writes": s_ins["ins_bucket_writes"]},
+                           "bucket_writes": s_ins["ins_bucket_writes"],
+                           "direct_reads": s_ins["ins_direct_reads"],
+                           "direct_writes": s_ins["ins_direct_writes"],
+                           "evict_keys": s_ins["ins_evict_keys"]},
                 "query": {"ops": W.n_queries, "s": t2 - t1,
                           "bucket_reads": s["qry_bucket_reads"], "bucket_writes": 0},
                 "delete": {"ops": W.n_deletes, "s": t3 - t2,
@@ -168,6 +171,28 @@ def oracle_run(W, repeat: int = 1):
                            "bucket_writes": s["rem_bucket_writes"]}})
         o.close()
     return res
+
+
+def kernel_bytes(phases: dict, bucket_bytes: int, n_insert: int, n_query: int,
+                 n_delete: int) -> dict:
+    """Algorithmic bytes per step of each kernel, from the oracle's bucket
+    counts (per operation) scaled to the workload's operation counts:
+    32-byte sectors of the buckets it reads and writes, plus 8 B of key and
+    1 B of flag per key it handles.  Insert phase 1 handles every key; phase
+    2 handles the keys whose two buckets were full (it re-reads the key)."""
+    spb = max(1, math.ceil(bucket_bytes / SECTOR)) * SECTOR
+    ins = phases["insert"]
+    per = ins["ops"]
+    d_touch = (ins["direct_reads"] + ins["direct_writes"]) / per
+    e_touch = (ins["bucket_reads"] + ins["bucket_writes"] - ins["direct_reads"]
+               - ins["direct_writes"]) / per
+    e_keys = ins["evict_keys"] / per
+    q = phases["query"]
+    d = phases["delete"]
+    return {"insert_direct": n_insert * (d_touch * spb + 9),
+            "insert_evict": n_insert * (e_touch * spb + 9 * e_keys),
+            "contains": n_query * (q["bucket_reads"] / q["ops"] * spb + 9),
+            "remove": n_delete * ((d["bucket_reads"] + d["bucket_writes"]) / d["ops"] * spb + 9)}
 
 
 def bytes_per_op(phases: dict, bucket_bytes: int) -> dict:
@@ -244,6 +269,8 @@ def gpu_arm(args):
     stream.synchronize()
     st = filt.stats()
 
+    filt.set_kernel_timing(True)
+    filt.kernel_times(reset=True)
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -267,6 +294,8 @@ def gpu_arm(args):
     clocks = sampler.stop() if sampler else None
 
     elapsed = t_start.elapsed_time(t_end) / 1e3
+    ktimes = filt.kernel_times(reset=True)
+    filt.set_kernel_timing(False)
     ops_local = float(W.ops_per_step()) * args.steps
     t_max, ops_all = reduce_max_sum(elapsed, ops_local)
     ph = {"insert": [], "query": [], "delete": []}
@@ -319,35 +348,72 @@ def gpu_arm(args):
         "clocks": clocks,
     }
 
-    # ---- roofline of the dominant phase + CPU baseline (rank 0, N=1 only) ----
+    # ---- roofline of the dominant kernel + CPU baseline (rank 0, N=1 only) ----
     peaks = load_peaks()
     cpu = None
-    bpo = None
+    S = workloads.BY_NAME[args.cpu_workload if (ws == 1 and not args.no_cpu)
+                          else "ref_2^20x4_f16_lf0.95"]
+    secs, ops, phases = oracle_run(S)
     if ws == 1 and not args.no_cpu:
-        S = workloads.BY_NAME[args.cpu_workload]
-        secs, ops, phases = oracle_run(S)
-        bpo = bytes_per_op(phases, W.f * W.b // 8)
         cpu = {"value": round(ops / secs / 1e6, 3), "unit": "Mops/s", "cores": 1,
                "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": (f"{S.name}: the same load-factor path, 50/50 query mix and "
                           f"delete fraction on {S.m} buckets ({ops} ops, {secs:.1f} s, "
                           "one thread of the host)"),
                "phases_mops": {k: round(p["ops"] / p["s"] / 1e6, 3) for k, p in phases.items()}}
-    if bpo is None:
-        bpo = {"insert": 73.0, "query": 57.0, "delete": 66.0}
-    dom = max(med, key=lambda k: med[k])
-    n_dom = {"insert": W.n_insert, "query": W.n_queries, "delete": W.n_deletes}
+    kb = kernel_bytes(phases, W.f * W.b // 8, W.n_insert, W.n_queries, W.n_deletes)
     peak = peaks.get("hbm_gbs") or 6800.0
-    ach = {k: n_dom[k] * bpo[k] / med[k] / 1e9 for k in med}
-    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach[dom], 1),
-                       "peak": peak, "unit": "GB/s",
-                       "frac": round(ach[dom] / peak, 4), "traffic": args.traffic,
-                       "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
-                       "bytes_per_op": {k: round(v, 2) for k, v in bpo.items()},
-                       "phases_frac": {k: round(v / peak, 4) for k, v in ach.items()}}
+    kern = {}
+    for k, (launches, ms) in ktimes.items():
+        if not launches:
+            continue
+        ach = kb[k] * args.steps / (ms / 1e3) / 1e9
+        kern[k] = {"launches": launches, "avg_launch_ms": round(ms / launches, 4),
+                   "total_ms_per_step": round(ms / args.steps, 3),
+                   "algorithmic_bytes_per_step": int(kb[k]),
+                   "achieved_GBps": round(ach, 1), "frac": round(ach / peak, 4)}
+    dom = max(kern, key=lambda k: kern[k]["total_ms_per_step"])
+    ceiling = random_gather_ceiling(stream)
+    out["roofline"] = {"bound": "hbm", "kernel": dom,
+                       "achieved": kern[dom]["achieved_GBps"], "peak": peak, "unit": "GB/s",
+                       "frac": kern[dom]["frac"], "traffic": args.traffic,
+                       "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
+                       if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
+                       "random_sector_ceiling_GBps": ceiling["GBps_32B"],
+                       "frac_of_random_sector_ceiling": round(
+                           kern[dom]["achieved_GBps"] / ceiling["GBps_32B"], 3),
+                       "kernels": kern,
+                       "bytes_per_op_model": "32 B x (distinct buckets read + written, "
+                                             "counted by the oracle on " + S.name + ") + 9 B"}
+    out["random_gather"] = ceiling
     out["cpu_baseline"] = cpu
     out["e2e"] = e2e
     return out
+
+
+def random_gather_ceiling(stream, n_access: int = 1 << 28):
+    """Random 8-byte loads over a 2 GiB buffer with the query kernel's load
+    instruction (cf_probe_gather): the rate HBM serves independent random
+    sectors, the real ceiling of every probe of the filter."""
+    import torch
+    from paper_2603_15486_gb300 import _lib
+    L = _lib.load()
+    buf = torch.zeros(1 << 31, dtype=torch.uint8, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sh = stream.cuda_stream
+    for _ in range(2):
+        L.cf_probe_gather(buf.data_ptr(), buf.numel(), n_access, 8, 8, 3, sink.data_ptr(), sh)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = L.cf_probe_gather(buf.data_ptr(), buf.numel(), n_access, 8, 8, 5, sink.data_ptr(), sh)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    del buf
+    g = n_access / ms / 1e6
+    return {"gloads_per_s": round(g, 2), "GBps_32B": round(g * 32, 1), "rc": rc,
+            "what": "2^28 random 8-byte loads over 2 GiB, 8 in flight per thread"}
 
 
 def e2e_run(filt, keys, queries, W, args, stream):
@@ -645,13 +711,123 @@ def serve_arm(args):
             "server": {"waves": st["waves"], "mean_wave_requests": round(st["completed"] / max(1, st["waves"]), 2)}}
 
 
+# ---------------------------------------------------------------------------
+# Ablations of the paper's Sec. 5.4 on the paper's geometry (f16, b = 16).
+# ---------------------------------------------------------------------------
+def ablation_arm(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2603_15486_gb300 import CuckooFilter
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def ev(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            pre = fn("pre")
+            e0.record(stream)
+            fn("run")
+            e1.record(stream)
+            stream.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    # Eviction policy (Fig. 5-6): 2^28 slots (2^24 buckets x 16), pre-fill
+    # 3/4 of the target, time the last quarter.
+    m, b = 1 << 24, 16
+    slots = m * b
+    keys = torch.empty(slots, dtype=torch.int64, device="cuda")
+    workloads.keys_dev(keys.data_ptr(), slots, 2, 0, sh)
+    stream.synchronize()
+    evict = {}
+    for pol in ("bfs", "dfs"):
+        g = CuckooFilter(m, 16, b, 500, eviction=pol)
+        rows = {}
+        for alpha in (0.75, 0.8, 0.85, 0.9, 0.95, 0.98, 1.0):
+            n = workloads.lf_count(m, b, alpha)
+            q = (3 * n) // 4
+            evc = torch.empty(n - q, dtype=torch.int32, device="cuda")
+            fl = torch.empty(n - q, dtype=torch.uint8, device="cuda")
+
+            def step(phase, q=q, n=n, evc=evc, fl=fl, g=g):
+                if phase == "pre":
+                    g.clear(stream=stream)
+                    g.insert(keys[:q], want_flags=False, stream=stream)
+                else:
+                    g.insert(keys[q:n], flags=fl, evictions=evc, stream=stream)
+            ms = ev(step)
+            e = evc.cpu().numpy()
+            rows[str(alpha)] = {"mops": round((n - q) / ms / 1e3, 1), "ms": round(ms, 3),
+                                "evictions_p90_p95_p99_max": [int(np.percentile(e, 90)),
+                                                              int(np.percentile(e, 95)),
+                                                              int(np.percentile(e, 99)),
+                                                              int(e.max())],
+                                "fails": int((fl != 1).sum())}
+        evict[pol] = rows
+        g.close()
+    # Bucket policy (Fig. 7): LF 0.95, L2-resident (2^22 slots) and
+    # DRAM-resident (2^28 slots); insert, query+, query-, delete.
+    policy = {}
+    for name, mm in (("L2_2^22_slots", 1 << 18), ("DRAM_2^28_slots", 1 << 24)):
+        n = workloads.lf_count(mm, b, 0.95)
+        pos = keys[:n]
+        neg = torch.empty(n, dtype=torch.int64, device="cuda")
+        workloads.keys_dev(neg.data_ptr(), n, 2, slots, sh)
+        out = torch.empty(n, dtype=torch.uint8, device="cuda")
+        res = {}
+        for pol in ("xor", "offset"):
+            g = CuckooFilter(mm, 16, b, 500, policy=pol)
+
+            def ins(phase, g=g):
+                if phase == "pre":
+                    g.clear(stream=stream)
+                else:
+                    g.insert(pos, flags=out, stream=stream)
+            t_ins = ev(ins)
+            fails = int((out != 1).sum())
+            t_qp = ev(lambda ph, g=g: ph == "run" and g.contains(pos, out=out, stream=stream))
+            found = int(out.sum())
+            t_qn = ev(lambda ph, g=g: ph == "run" and g.contains(neg, out=out, stream=stream))
+            fpc = int(out.sum())
+
+            def rem(phase, g=g):
+                if phase == "pre":
+                    g.clear(stream=stream)
+                    g.insert(pos, want_flags=False, stream=stream)
+                else:
+                    g.remove(pos, out=out, stream=stream)
+            t_rm = ev(rem)
+            res[pol] = {"insert_mops": round(n / t_ins / 1e3, 1),
+                        "query_pos_mops": round(n / t_qp / 1e3, 1),
+                        "query_neg_mops": round(n / t_qn / 1e3, 1),
+                        "delete_mops": round(n / t_rm / 1e3, 1),
+                        "insert_fails": fails, "query_pos_found": found, "n": n,
+                        "fpr": round(fpc / n, 7)}
+            g.close()
+        policy[name] = res
+    return {"metric": "ablations: BFS vs DFS eviction (Fig. 5-6 protocol), XOR vs Offset "
+                      "bucket policy (Fig. 7 protocol)", "mode": "ablation", "unit": "Mops/s",
+            "value": policy["DRAM_2^28_slots"]["xor"]["insert_mops"], "n_gpus": 1,
+            "higher_is_better": True,
+            "config": {"geometry": "f16, b = 16", "eviction_table": "2^28 slots (2^24 buckets)",
+                       "eviction_protocol": "pre-fill 3/4 of the target load, time the last 1/4",
+                       "policy_load_factor": 0.95},
+            "eviction": evict, "bucket_policy": policy}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["main", "batched", "serve"], default="main",
+    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation"], default="main",
                     help="main: the large-filter headline; batched / serve: the "
                          "many-filters and serving workloads (one JSON line each)")
     ap.add_argument("--serve-requests", type=int, default=4000)
@@ -673,6 +849,8 @@ def main(argv=None):
         out = batched_arm(args)
     elif args.mode == "serve":
         out = serve_arm(args)
+    elif args.mode == "ablation":
+        out = ablation_arm(args)
     else:
         out = gpu_arm(args)
     if out is not None:

@@ -100,8 +100,9 @@ typedef struct {
   uint64_t remove_fail;
   uint64_t evictions;      /* slot overwrites inside eviction loops         */
   uint64_t victims;        /* tags dropped (may exceed the log capacity)    */
-  uint64_t rollbacks;      /* BFS relocations undone after a lost CAS       */
-  uint64_t rollback_lost;  /* rollbacks whose copy was already gone         */
+  uint64_t rollbacks;      /* undone BFS moves: always 0 (a move swaps the
+                              new tag in first, so nothing is ever undone) */
+  uint64_t rollback_lost;  /* always 0, as rollbacks                        */
   uint64_t contention;     /* bounded CAS loops that ran out                */
   uint32_t error_word;     /* bit 0: contention; bit 1: victim log full     */
   uint32_t victim_capacity;
@@ -392,6 +393,19 @@ cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
                             uint8_t* out_flags, void* stream);
 
 /* ---- measurement helpers ------------------------------------------------ */
+/* Per-kernel device time of one filter's single-filter calls: while enabled,
+ * an event pair is recorded on the launching stream around every kernel
+ * launch.  Index 0: insert phase 1 (direct insertion into i1 / i2), 1:
+ * insert phase 2 (eviction loop), 2: contains, 3: remove.
+ * cf_read_kernel_times waits for the recorded events, sums their elapsed
+ * times and (reset != 0) recycles them. */
+typedef struct {
+  uint64_t launches[4];
+  double ms[4];
+} cf_kernel_times;
+cf_status cf_set_kernel_timing(cf_filter* f, int enable);
+cf_status cf_read_kernel_times(cf_filter* f, cf_kernel_times* out, int reset);
+
 /* Random-gather ceiling: n_access independent loads of access_bytes (8, 16
  * or 32) at pseudo-random aligned offsets within the first power-of-two
  * part of the device buffer `buf` (32-byte aligned), with the load

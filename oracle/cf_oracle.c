@@ -452,9 +452,12 @@ int cfo_insert(cfo_filter* F, uint64_t key, uint32_t* evictions) {
       ok = 1;
     }
   }
+  F->st.ins_direct_reads += F->n_r;
+  F->st.ins_direct_writes += F->n_w;
   if (!ok) {
     uint32_t vt = t1;
     uint64_t vb = i1;
+    F->st.ins_evict_keys++;
     if (F->max_ev > 0) {
       uint64_t rng = h;
       int first = (rng_next(&rng) & 1) == 0;

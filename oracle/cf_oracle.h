@@ -50,6 +50,10 @@ typedef struct {
   uint64_t qry_bucket_reads;   /* buckets probed by Alg. 2 with short-circuit*/
   uint64_t rem_bucket_reads;   /* buckets probed by Alg. 3 with short-circuit*/
   uint64_t rem_bucket_writes;  /* buckets written by successful removes      */
+  /* The insert counters split by phase of Alg. 1: direct insertion into i1
+   * / i2, and the eviction loop (distinct buckets first touched there). */
+  uint64_t ins_direct_reads, ins_direct_writes;
+  uint64_t ins_evict_keys;     /* keys that entered the eviction loop        */
 } cfo_stats;
 
 /* Returns NULL on invalid parameters or allocation failure. */

@@ -61,7 +61,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "occupancy", "insert_ok", "insert_fail", "remove_ok", "remove_fail",
         "evictions", "victims", "ins_bucket_reads", "ins_bucket_writes",
-        "qry_bucket_reads", "rem_bucket_reads", "rem_bucket_writes")]
+        "qry_bucket_reads", "rem_bucket_reads", "rem_bucket_writes",
+        "ins_direct_reads", "ins_direct_writes", "ins_evict_keys")]
 
 
 def lib():

@@ -64,6 +64,13 @@ class CfServerStats(ctypes.Structure):
         ("live_filters", ctypes.c_uint32), ("pending_filters", ctypes.c_uint32)]
 
 
+class CfKernelTimes(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 4), ("ms", ctypes.c_double * 4)]
+
+
+KERNEL_KINDS = ("insert_direct", "insert_evict", "contains", "remove")
+
+
 # Every symbol include/cf.h declares, with (restype, argtypes).
 _vp, _u64, _u32, _int = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
 _st = ctypes.c_int
@@ -119,6 +126,8 @@ SIGNATURES = {
     "cf_batch_set_variant": (_st, [_vp, _u32]),
     "cf_batch_get_tuning": (_st, [_vp, ctypes.POINTER(CfTuning)]),
     "cf_batch_variant_count": (_u32, [_vp]),
+    "cf_set_kernel_timing": (_st, [_vp, _int]),
+    "cf_read_kernel_times": (_st, [_vp, ctypes.POINTER(CfKernelTimes), _int]),
     "cf_probe_gather": (_st, [_vp, _u64, _u64, _u32, _u32, _u64, _vp, _vp]),
     "cf_set_l2_fetch_granularity": (_st, [_u32]),
     "cf_get_l2_fetch_granularity": (_st, [ctypes.POINTER(_u32)]),

@@ -252,9 +252,9 @@ cf_status run_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
                  uint8_t* flags, uint32_t* evout, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (op == OP_CONTAINS) {
-    e = f->ops->contains(f->d, keys, n, flags, s);
+    e = f->ops->contains(f->d, keys, n, flags, s, f->timer);
   } else if (op == OP_REMOVE) {
-    e = f->ops->remove(f->d, keys, n, flags, s);
+    e = f->ops->remove(f->d, keys, n, flags, s, f->timer);
   } else {
     cf_status st = ensure_queue(f, n);
     if (st != CF_OK) return st;
@@ -262,7 +262,8 @@ cf_status run_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
       const uint64_t len = (n - off) < kInsertChunk ? (n - off) : kInsertChunk;
       e = f->ops->insert_chunk(f->d, keys + off, uint32_t(len),
                                flags ? flags + off : nullptr,
-                               evout ? evout + off : nullptr, f->queue, s);
+                               evout ? evout + off : nullptr, f->queue, s,
+                               f->timer);
     }
   }
   if (e != cudaSuccess) {
@@ -341,6 +342,40 @@ constexpr size_t kSnapHdr = 64;
 extern "C" {
 
 const char* cf_last_error(void) { return g_err; }
+
+cf_status cf_set_kernel_timing(cf_filter* f, int enable) {
+  if (!f) return CF_EINVAL;
+  if (enable && !f->timer) f->timer = new cfk::FilterTimer();
+  if (!enable && f->timer) {
+    if (f->has_last) cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev);
+    delete f->timer;
+    f->timer = nullptr;
+  }
+  return CF_OK;
+}
+
+cf_status cf_read_kernel_times(cf_filter* f, cf_kernel_times* out, int reset) {
+  if (!f || !out) return CF_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  if (!f->timer) return CF_OK;
+  for (auto& r : f->timer->recs) {
+    CF_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    CF_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    if (r.kind >= 0 && r.kind < 4) {
+      out->launches[r.kind] += 1;
+      out->ms[r.kind] += ms;
+    }
+  }
+  if (reset) {
+    for (auto& r : f->timer->recs) {
+      f->timer->pool.push_back(r.a);
+      f->timer->pool.push_back(r.b);
+    }
+    f->timer->recs.clear();
+  }
+  return CF_OK;
+}
 
 int cf_version(void) { return 10000; }
 
@@ -428,6 +463,7 @@ cf_status cf_destroy(cf_filter* f) {
   free_staging(f);
   if (f->queue) cudaFree(f->queue);
   if (f->last_ev) cudaEventDestroy(f->last_ev);
+  delete f->timer;
   if (f->owns && f->mem) cudaFree(f->mem);
   delete f;
   return CF_OK;

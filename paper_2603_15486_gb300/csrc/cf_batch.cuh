@@ -35,7 +35,7 @@ struct BatchCtl {
   uint64_t n_tiles;
   unsigned long long next_tile;
   unsigned int queue_count;
-  unsigned int pad0;
+  unsigned int evict_next;  // next eviction-queue entry to hand out
   unsigned long long pad[4];
 };
 static_assert(sizeof(BatchCtl) == 64, "batch header is 64 bytes");
@@ -113,32 +113,73 @@ k_batch_tiles(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
   }
 }
 
+// The combined eviction queue of all inserting items, with the lane
+// refill of k_insert_evict: each warp iteration runs one round of every
+// lane's chain; lanes whose chain ended take the next queued key.
 template <class G, int FW, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-k_batch_evict(const BatchCtl* ctl, const BatchItemDev* __restrict__ items,
+k_batch_evict(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
               const uint2* __restrict__ queue) {
   const uint32_t qn = *reinterpret_cast<const volatile unsigned int*>(&ctl->queue_count);
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < qn;
-       e += gridDim.x * blockDim.x) {
-    const uint2 q = queue[e];
-    const BatchItemDev& I = items[q.x];
-    const DevFilter d = I.d;
-    EvictCounters ec;
-    uint32_t ev = 0;
-    const int r = evict_one<G, FW>(d, I.keys[q.y], q.y, I.flags, nullptr, ev, ec);
-    if (r == EV_OK) {
-      atomicAdd(&d.ctrl->occupancy, 1ull);
-      atomicAdd(&d.ctrl->insert_ok, 1ull);
-    } else {
-      atomicAdd(&d.ctrl->insert_fail, 1ull);
+  const uint32_t lane = threadIdx.x & 31;
+  Chain<G> c{};
+  uint2 q{};
+  bool active = false, dry = false;
+  for (;;) {
+    if (!dry) {
+      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
+      if (need) {
+        const int leader = __ffs(need) - 1;
+        uint32_t base = 0;
+        if (int(lane) == leader) base = atomicAdd(&ctl->evict_next, __popc(need));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (base + __popc(need) >= qn) dry = true;
+        if (!active) {
+          const uint32_t e = base + __popc(need & ((1u << lane) - 1u));
+          if (e < qn) {
+            q = queue[e];
+            const BatchItemDev& I = items[q.x];
+            const DevFilter d = I.d;
+            const KeyHash kh = hash_key<G>(d, I.keys[q.y]);
+            if (d.max_ev == 0) {
+              log_victim(d, kh.fp, kh.i1);
+              if (I.flags) st_flag(I.flags + q.y, EV_FAIL);
+              atomicAdd(&d.ctrl->insert_fail, 1ull);
+            } else {
+              c = chain_start<G>(d, kh);
+              active = true;
+            }
+          }
+        }
+      }
     }
-    if (ev) atomicAdd(&d.ctrl->evictions, (unsigned long long)ev);
-    if (ec.rollbacks) atomicAdd(&d.ctrl->rollbacks, (unsigned long long)ec.rollbacks);
-    if (ec.rollback_lost)
-      atomicAdd(&d.ctrl->rollback_lost, (unsigned long long)ec.rollback_lost);
-    if (ec.contention) {
-      atomicAdd(&d.ctrl->contention, (unsigned long long)ec.contention);
-      atomicOr(&d.ctrl->error_word, 1u);
+    if (!__any_sync(0xFFFFFFFFu, active)) {
+      if (dry) break;
+      continue;
+    }
+    if (active) {
+      const BatchItemDev& I = items[q.x];
+      const DevFilter d = I.d;
+      EvictCounters ec;
+      uint32_t vt = 0;
+      uint64_t vb = 0;
+      const int r = evict_round<G, FW>(d, c, vt, vb, ec);
+      if (ec.contention) {
+        atomicAdd(&d.ctrl->contention, (unsigned long long)ec.contention);
+        atomicOr(&d.ctrl->error_word, 1u);
+      }
+      if (r != ROUND_CONTINUE) {
+        if (r != EV_OK) log_victim(d, vt, vb);
+        if (I.flags) st_flag(I.flags + q.y, uint8_t(r));
+        if (r == EV_OK) {
+          atomicAdd(&d.ctrl->occupancy, 1ull);
+          atomicAdd(&d.ctrl->insert_ok, 1ull);
+        } else {
+          atomicAdd(&d.ctrl->insert_fail, 1ull);
+        }
+        if (c.ev) atomicAdd(&d.ctrl->evictions, (unsigned long long)c.ev);
+        active = false;
+      }
     }
   }
 }
@@ -152,7 +193,7 @@ struct BatchVariant {
   const void* evict_fn;
   cudaError_t (*tiles)(BatchCtl*, const BatchItemDev*, const uint64_t*, uint2*,
                        unsigned, cudaStream_t);
-  cudaError_t (*evict)(const BatchCtl*, const BatchItemDev*, const uint2*,
+  cudaError_t (*evict)(BatchCtl*, const BatchItemDev*, const uint2*,
                        unsigned, cudaStream_t);
 };
 
@@ -164,7 +205,7 @@ struct BatchLaunch {
     k_batch_tiles<G, K, BLOCK><<<grid, BLOCK, 0, s>>>(c, it, b, q);
     return cudaGetLastError();
   }
-  static cudaError_t evict(const BatchCtl* c, const BatchItemDev* it,
+  static cudaError_t evict(BatchCtl* c, const BatchItemDev* it,
                            const uint2* q, unsigned grid, cudaStream_t s) {
     k_batch_evict<G, FW, kBlock><<<grid, kBlock, 0, s>>>(c, it, q);
     return cudaGetLastError();

@@ -414,204 +414,218 @@ struct EvictCounters {
 // Result codes of the eviction loops (the key's flag).
 enum : int { EV_FAIL = 0, EV_OK = 1, EV_CONTENTION = 2 };
 
-// BFS eviction heuristic (Sec. 4.6.1).  Starts with `tag` destined for the
-// full bucket `cur`, whose words the caller passes in `bk`.  Each round
-// inspects b/2 consecutive slots from a random start; if some candidate's
-// alternate bucket has an empty slot, the candidate is moved there and the
-// new tag takes its slot (two steps, the first undone if the second CAS
-// finds the slot changed).  Otherwise the last candidate is swapped out and
-// the search restarts from its alternate bucket.
-// Memory round trips per round: the b/2 alternate-bucket probes are issued
-// together; the relocation CASes into the probed words directly; after a
-// swap, the words loaded by the direct-insert attempt in the new bucket
-// serve the next round.
-template <class G, int FW = G::B / 2>
-__device__ int evict_bfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
-                         uint32_t tag, Bucket<G> bk, uint32_t& ev,
-                         uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
+// State of one key's eviction chain between rounds: the tag in hand, the
+// bucket it is destined for (and that bucket's words as last seen), the
+// key's random stream and the overwrites so far.
+template <class G>
+struct Chain {
+  uint64_t rng;
+  uint64_t cur;
+  uint32_t tag;
+  uint32_t ev;
+  Bucket<G> bk;
+};
+
+// A round that neither placed the tag nor gave up.
+constexpr int ROUND_CONTINUE = -1;
+
+// One round of the BFS eviction heuristic (Sec. 4.6.1), for a tag destined
+// for the full bucket c.cur.  The round inspects b/2 consecutive slots from
+// a random start and probes their alternate buckets.  If some candidate's
+// alternate has an empty slot, the first such candidate (in order) moves
+// there and the new tag takes its slot; otherwise the last candidate is
+// evicted and the chain continues from its alternate bucket.
+//
+// Order of the two writes of a move: the paper inserts the candidate into
+// its alternate first and then CASes the new tag over it, undoing the
+// insert if that CAS finds the slot changed.  Under contention the undo can
+// miss (another thread may have carried the copy on already) and leave a
+// duplicate.  Here the new tag is CASed into the candidate's slot first
+// (taking whatever that slot holds at that moment), then the evicted tag is
+// inserted into its alternate bucket, using the words the probe loaded.  If
+// that bucket lost its room meanwhile, the evicted tag stays in hand and
+// the chain goes on from there.  A tag is never duplicated or lost; run by
+// one thread, both orders leave the same table.
+//
+// FW alternate buckets (the frontier) are probed together per group,
+// groups in candidate order; the choice does not depend on FW.
+// Returns EV_OK, EV_CONTENTION (vt/vb = the tag dropped and its bucket) or
+// ROUND_CONTINUE.  Precondition: c.ev < max_evictions.
+template <class G, int FW>
+__device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
+                         uint64_t& vb, EvictCounters& ec) {
   using W = typename G::Word;
   constexpr int H = G::B / 2;
   static_assert(FW >= 1 && H % FW == 0, "frontier width divides b/2");
-  while (ev < d.max_ev) {
-    const uint32_t start = uint32_t(rng_next(rng) & (G::B - 1));
-    W* cbase = bucket_ptr<G>(d, cur);
-    if (has_empty<G>(bk)) {
-      // Only reachable under concurrency (a slot freed by a rollback).
-      const int r = try_insert_loaded<G>(d, cur, tag, bk);
-      if (r == TI_OK) return EV_OK;
-    }
-    uint32_t t[H], mv[H];
-    uint64_t a[H];
-    bool cand[H];
+  const uint32_t start = uint32_t(rng_next(c.rng) & (G::B - 1));
+  W* cbase = bucket_ptr<G>(d, c.cur);
+  if (has_empty<G>(c.bk)) {
+    // Only reachable under concurrency (a slot freed by a delete).
+    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk) == TI_OK) return EV_OK;
+  }
+  uint32_t t[H], mv[H];
+  uint64_t a[H];
+  bool cand[H];
 #pragma unroll
-    for (int k = 0; k < H; ++k) {
-      t[k] = get_slot<G>(bk, (start + k) & (G::B - 1));
-      a[k] = alt_of<G>(d, cur, t[k], mv[k]);
-      cand[k] = t[k] != 0 && a[k] != cur;
-    }
-    // The frontier: FW alternate buckets probed together per group, groups
-    // in candidate order; the first candidate (in order) whose alternate
-    // bucket has room is relocated, whatever FW is.
+  for (int k = 0; k < H; ++k) {
+    t[k] = get_slot<G>(c.bk, (start + k) & (G::B - 1));
+    a[k] = alt_of<G>(d, c.cur, t[k], mv[k]);
+    cand[k] = t[k] != 0 && a[k] != c.cur;
+  }
+  int chosen = H - 1;
+  bool open = false;
+  Bucket<G> tb{};
 #pragma unroll
-    for (int g = 0; g < H; g += FW) {
-      Bucket<G> ab[FW];
-      bool open[FW];
+  for (int g = 0; g < H; g += FW) {
+    if (open) break;
+    Bucket<G> ab[FW];
 #pragma unroll
-      for (int q = 0; q < FW; ++q)
-        if (cand[g + q]) ab[q] = load_bucket<G, false>(bucket_ptr<G>(d, a[g + q]));
+    for (int q = 0; q < FW; ++q)
+      if (cand[g + q]) ab[q] = load_bucket<G, false>(bucket_ptr<G>(d, a[g + q]));
 #pragma unroll
-      for (int q = 0; q < FW; ++q) open[q] = cand[g + q] && has_empty<G>(ab[q]);
-#pragma unroll 1
-      for (int q = 0; q < FW; ++q) {
-        if (!open[q]) continue;
-        const int k = g + q;
-        Bucket<G> tb = ab[0];
-#pragma unroll
-        for (int z = 1; z < FW; ++z)
-          if (z == q) tb = ab[z];
-        const int r = try_insert_loaded<G>(d, a[k], mv[k], tb);
-        if (r != TI_OK) {
-          if (r == TI_CONTENTION) ec.contention++;
-          continue;
-        }
-        const uint32_t c = (start + k) & (G::B - 1);
-        const int wi = int(c / G::kTpw), lane = int(c % G::kTpw);
-        W w = select_word<G>(bk, wi);
-        bool placed = false;
-        for (int tries = 0; tries < kMaxCas; ++tries) {
-          if (get_lane<G>(w, lane) != t[k]) break;  // the slot changed
-          const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, tag));
-          if (old == w) {
-            placed = true;
-            break;
-          }
-          w = old;
-        }
-        if (placed) {
-          ev++;
-          return EV_OK;
-        }
-        // Undo step 1: remove one copy of the candidate from its alternate
-        // bucket, or from the bucket it may have been moved back to.
-        ec.rollbacks++;
-        if (try_remove<G>(d, a[k], mv[k]) != TI_OK) {
-          uint32_t back;
-          const uint64_t aa = alt_of<G>(d, a[k], mv[k], back);
-          if (try_remove<G>(d, aa, back) != TI_OK) ec.rollback_lost++;
-        }
-        bk = load_bucket<G, false>(cbase);
+    for (int q = 0; q < FW; ++q) {
+      if (!open && cand[g + q] && has_empty<G>(ab[q])) {
+        open = true;
+        chosen = g + q;
+        tb = ab[q];
       }
-    }
-    // No shallow path: swap the last candidate out.
-    const uint32_t c = (start + H - 1) & (G::B - 1);
-    const int wi = int(c / G::kTpw), lane = int(c % G::kTpw);
-    W w = select_word<G>(bk, wi);
-    bool swapped = false;
-    uint32_t evicted = 0;
-    for (int tries = 0; tries < kMaxCas; ++tries) {
-      const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, tag));
-      if (old == w) {
-        evicted = get_lane<G>(w, lane);
-        swapped = true;
-        break;
-      }
-      w = old;
-    }
-    if (!swapped) {
-      ec.contention++;
-      vt = tag;
-      vb = cur;
-      return EV_CONTENTION;
-    }
-    ev++;
-    if (evicted == 0) return EV_OK;
-    uint32_t moved;
-    cur = alt_of<G>(d, cur, evicted, moved);
-    tag = moved;
-    bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
-    const int r = try_insert_loaded<G>(d, cur, tag, bk);
-    if (r == TI_OK) return EV_OK;
-    if (r == TI_CONTENTION) {
-      ec.contention++;
-      vt = tag;
-      vb = cur;
-      return EV_CONTENTION;
     }
   }
-  vt = tag;
-  vb = cur;
-  return EV_FAIL;
+  // Swap the new tag into the chosen slot.
+  const uint32_t sl = (start + uint32_t(chosen)) & (G::B - 1);
+  const int wi = int(sl / G::kTpw), lane = int(sl % G::kTpw);
+  W w = select_word<G>(c.bk, wi);
+  bool swapped = false;
+  uint32_t evicted = 0;
+  for (int tries = 0; tries < kMaxCas; ++tries) {
+    const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, c.tag));
+    if (old == w) {
+      evicted = get_lane<G>(w, lane);
+      swapped = true;
+      break;
+    }
+    w = old;
+  }
+  if (!swapped) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  c.ev++;
+  if (evicted == 0) return EV_OK;
+  // Carry the evicted tag to its alternate bucket and insert it there.
+  uint32_t moved;
+  c.cur = alt_of<G>(d, c.cur, evicted, moved);
+  c.tag = moved;
+  if (open && evicted == t[chosen])
+    c.bk = tb;  // the probe's words of that very bucket
+  else
+    c.bk = load_bucket<G, false>(bucket_ptr<G>(d, c.cur));
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk);
+  if (r == TI_OK) return EV_OK;
+  if (r == TI_CONTENTION) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  return ROUND_CONTINUE;
 }
 
-// Greedy DFS chain (Alg. 1 phase 2): swap the tag into a random slot of cur,
-// carry the evicted tag to its alternate bucket, try a direct insert there.
-// The words loaded by that attempt serve the next swap.
+// One round of the greedy DFS chain (Alg. 1 phase 2): swap the tag into a
+// random slot of c.cur, carry the evicted tag to its alternate bucket, try a
+// direct insert there; the words loaded by that attempt serve the next
+// round.  Same returns and precondition as bfs_round.
 template <class G>
-__device__ int evict_dfs(const DevFilter& d, uint64_t& rng, uint64_t cur,
-                         uint32_t tag, Bucket<G> bk, uint32_t& ev,
-                         uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
+__device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
+                         uint64_t& vb, EvictCounters& ec) {
   using W = typename G::Word;
-  while (ev < d.max_ev) {
-    const uint32_t s = uint32_t(rng_next(rng) & (G::B - 1));
-    const int wi = int(s / G::kTpw), lane = int(s % G::kTpw);
-    W* wp = bucket_ptr<G>(d, cur) + wi;
-    W w = select_word<G>(bk, wi);
-    bool swapped = false;
-    uint32_t evicted = 0;
-    for (int tries = 0; tries < kMaxCas; ++tries) {
-      const W old = atomicCAS(wp, w, replace_lane<G>(w, lane, tag));
-      if (old == w) {
-        evicted = get_lane<G>(w, lane);
-        swapped = true;
-        break;
-      }
-      w = old;
+  const uint32_t s = uint32_t(rng_next(c.rng) & (G::B - 1));
+  const int wi = int(s / G::kTpw), lane = int(s % G::kTpw);
+  W* wp = bucket_ptr<G>(d, c.cur) + wi;
+  W w = select_word<G>(c.bk, wi);
+  bool swapped = false;
+  uint32_t evicted = 0;
+  for (int tries = 0; tries < kMaxCas; ++tries) {
+    const W old = atomicCAS(wp, w, replace_lane<G>(w, lane, c.tag));
+    if (old == w) {
+      evicted = get_lane<G>(w, lane);
+      swapped = true;
+      break;
     }
-    if (!swapped) {
-      ec.contention++;
-      vt = tag;
-      vb = cur;
-      return EV_CONTENTION;
-    }
-    ev++;
-    if (evicted == 0) return EV_OK;
-    uint32_t moved;
-    cur = alt_of<G>(d, cur, evicted, moved);
-    tag = moved;
-    bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
-    const int r = try_insert_loaded<G>(d, cur, tag, bk);
-    if (r == TI_OK) return EV_OK;
-    if (r == TI_CONTENTION) {
-      ec.contention++;
-      vt = tag;
-      vb = cur;
-      return EV_CONTENTION;
-    }
+    w = old;
   }
-  vt = tag;
-  vb = cur;
-  return EV_FAIL;
+  if (!swapped) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  c.ev++;
+  if (evicted == 0) return EV_OK;
+  uint32_t moved;
+  c.cur = alt_of<G>(d, c.cur, evicted, moved);
+  c.tag = moved;
+  c.bk = load_bucket<G, false>(bucket_ptr<G>(d, c.cur));
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk);
+  if (r == TI_OK) return EV_OK;
+  if (r == TI_CONTENTION) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  return ROUND_CONTINUE;
 }
 
-// Phase 2 of Alg. 1 for one key whose direct insertion failed: pick i1 or
-// i2 with the key's first random draw, then run the eviction loop.
+// Start of phase 2 of Alg. 1 for a key whose two buckets were full: the
+// key's first random draw picks i1 or i2, whose words are loaded.
+template <class G>
+__device__ __forceinline__ Chain<G> chain_start(const DevFilter& d,
+                                                const KeyHash& kh) {
+  Chain<G> c;
+  c.rng = kh.h;
+  const bool first = (rng_next(c.rng) & 1) == 0;
+  c.cur = first ? kh.i1 : kh.i2;
+  c.tag = first ? kh.fp : (kh.fp | G::kChoice);
+  c.ev = 0;
+  c.bk = load_bucket<G, false>(bucket_ptr<G>(d, c.cur));
+  return c;
+}
+
+// One round of the filter's eviction policy, or EV_FAIL when the chain has
+// used max_evictions overwrites (the tag in hand is the victim).
+template <class G, int FW = G::B / 2>
+__device__ __forceinline__ int evict_round(const DevFilter& d, Chain<G>& c,
+                                           uint32_t& vt, uint64_t& vb,
+                                           EvictCounters& ec) {
+  if (c.ev >= d.max_ev) {
+    vt = c.tag;
+    vb = c.cur;
+    return EV_FAIL;
+  }
+  return d.eviction == 1 ? dfs_round<G>(d, c, vt, vb, ec)
+                         : bfs_round<G, FW>(d, c, vt, vb, ec);
+}
+
+// Phase 2 of Alg. 1 for one key, run to the end by one thread.
 template <class G, int FW = G::B / 2>
 __device__ int evict_key(const DevFilter& d, const KeyHash& kh, uint32_t& ev,
                          uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
-  const uint32_t t1 = kh.fp, t2 = kh.fp | G::kChoice;
   ev = 0;
   if (d.max_ev == 0) {
-    vt = t1;
+    vt = kh.fp;
     vb = kh.i1;
     return EV_FAIL;
   }
-  uint64_t rng = kh.h;
-  const bool first = (rng_next(rng) & 1) == 0;
-  const uint64_t cur = first ? kh.i1 : kh.i2;
-  const uint32_t tag = first ? t1 : t2;
-  const Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, cur));
-  return d.eviction == 1 ? evict_dfs<G>(d, rng, cur, tag, bk, ev, vt, vb, ec)
-                         : evict_bfs<G, FW>(d, rng, cur, tag, bk, ev, vt, vb, ec);
+  Chain<G> c = chain_start<G>(d, kh);
+  int r;
+  do {
+    r = evict_round<G, FW>(d, c, vt, vb, ec);
+  } while (r == ROUND_CONTINUE);
+  ev = c.ev;
+  return r;
 }
 
 __device__ __forceinline__ void log_victim(const DevFilter& d, uint32_t tag,

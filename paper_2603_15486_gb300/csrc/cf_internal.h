@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "cf.h"
 #include "cf_kernels.cuh"
@@ -31,6 +32,47 @@ cudaEvent_t pooled_event();
 void set_error(const char* what, cudaError_t e);
 void set_error_text(const char* text);
 
+// Per-filter kernel timer: an event pair recorded around every launch while
+// enabled; read (and recycled) by cf_read_kernel_times.
+struct FilterTimer final : KernelTimer {
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int open_kind = -1;
+  cudaEvent_t open_a = nullptr;
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int kind, cudaStream_t s) override {
+    open_kind = kind;
+    open_a = take();
+    cudaEventRecord(open_a, s);
+  }
+  void end(int kind, cudaStream_t s) override {
+    cudaEvent_t b = take();
+    cudaEventRecord(b, s);
+    recs.push_back(Rec{kind, open_a, b});
+    open_a = nullptr;
+  }
+  ~FilterTimer() override {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace cfk
 
 struct cf_filter {
@@ -51,5 +93,6 @@ struct cf_filter {
   cfk::Stage stage[2];
   cudaStream_t s_in = nullptr, s_out = nullptr;
   bool stage_ready = false;
+  cfk::FilterTimer* timer = nullptr;  // non-null while kernel timing is on
 };
 

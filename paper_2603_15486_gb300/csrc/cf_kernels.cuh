@@ -406,22 +406,69 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
   block_add(&d.ctrl->contention, c.cont);
 }
 
-// Insert, phase 2: the eviction loop for every queued key.  The queue length
-// is read on the device, so no host round trip separates the two phases.
-// The last block to finish resets the queue for the next batch.
+// Insert, phase 2: the eviction loop for every queued key.  Chains have
+// very different lengths, so a lane does not run one chain to its end:
+// every warp iteration runs ONE round of each lane's chain, and lanes whose
+// chain ended take the next queued key (one atomic per warp).  Warps stay
+// full until the queue runs dry instead of waiting for their longest chain.
+// The queue length is read on the device, so no host round trip separates
+// the two phases; the last block to finish resets the queue.
 template <class G>
 __global__ void __launch_bounds__(kBlock)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
                uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
                const uint32_t* __restrict__ queue) {
   const uint32_t qn = *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
+  const uint32_t lane = threadIdx.x & 31;
   uint32_t n_ok = 0, n_fail = 0, n_ev = 0;
   EvictCounters ec;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < qn;
-       e += gridDim.x * blockDim.x) {
-    const uint32_t i = queue[e];
-    const int r = evict_one<G>(d, keys[i], i, flags, evout, n_ev, ec);
-    if (r == EV_OK) n_ok++; else n_fail++;
+  Chain<G> c{};
+  uint32_t idx = 0;
+  bool active = false, dry = false;
+  for (;;) {
+    if (!dry) {
+      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
+      if (need) {
+        const int leader = __ffs(need) - 1;
+        uint32_t base = 0;
+        if (int(lane) == leader) base = atomicAdd(&d.ctrl->evict_next, __popc(need));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (base + __popc(need) >= qn) dry = true;
+        if (!active) {
+          const uint32_t e = base + __popc(need & ((1u << lane) - 1u));
+          if (e < qn) {
+            idx = queue[e];
+            const KeyHash kh = hash_key<G>(d, keys[idx]);
+            if (d.max_ev == 0) {
+              log_victim(d, kh.fp, kh.i1);
+              if (flags) st_flag(flags + idx, EV_FAIL);
+              if (evout) evout[idx] = 0;
+              n_fail++;
+            } else {
+              c = chain_start<G>(d, kh);
+              active = true;
+            }
+          }
+        }
+      }
+    }
+    if (!__any_sync(0xFFFFFFFFu, active)) {
+      if (dry) break;
+      continue;
+    }
+    if (active) {
+      uint32_t vt = 0;
+      uint64_t vb = 0;
+      const int r = evict_round<G>(d, c, vt, vb, ec);
+      if (r != ROUND_CONTINUE) {
+        if (r != EV_OK) log_victim(d, vt, vb);
+        if (flags) st_flag(flags + idx, uint8_t(r));
+        if (evout) evout[idx] = c.ev;
+        n_ev += c.ev;
+        if (r == EV_OK) n_ok++; else n_fail++;
+        active = false;
+      }
+    }
   }
   block_add(&d.ctrl->occupancy, n_ok);
   block_add(&d.ctrl->insert_ok, n_ok);
@@ -436,6 +483,7 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
     const unsigned prev = atomicAdd(&d.ctrl->done_blocks, 1u);
     if (prev == gridDim.x - 1) {
       d.ctrl->queue_count = 0;
+      d.ctrl->evict_next = 0;
       d.ctrl->done_blocks = 0;
       __threadfence();
     }
@@ -565,35 +613,61 @@ inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
   return unsigned(need < cap ? need : cap);
 }
 
+// Optional per-launch timing: the host side records CUDA events around each
+// kernel launch on the launching stream (cf_set_kernel_timing).
+enum KernelKind : int {
+  KK_INSERT_DIRECT = 0,
+  KK_INSERT_EVICT = 1,
+  KK_CONTAINS = 2,
+  KK_REMOVE = 3,
+  KK_NUM = 4
+};
+struct KernelTimer {
+  virtual void begin(int kind, cudaStream_t s) = 0;
+  virtual void end(int kind, cudaStream_t s) = 0;
+  virtual ~KernelTimer() = default;
+};
+
 template <class G>
 struct Launch {
   static constexpr int KQ = Tiles<G, false>::K;
   static constexpr int KM = Tiles<G, true>::K;
 
   static cudaError_t contains(const DevFilter& d, const uint64_t* keys,
-                              uint64_t n, uint8_t* flags, cudaStream_t s) {
+                              uint64_t n, uint8_t* flags, cudaStream_t s,
+                              KernelTimer* t) {
     auto fn = k_contains<G, KQ>;
+    if (t) t->begin(KK_CONTAINS, s);
     fn<<<persistent_grid(fn, n, kBlock * KQ), kBlock, 0, s>>>(d, keys, n, flags);
+    if (t) t->end(KK_CONTAINS, s);
     return cudaGetLastError();
   }
   static cudaError_t remove(const DevFilter& d, const uint64_t* keys,
-                            uint64_t n, uint8_t* flags, cudaStream_t s) {
+                            uint64_t n, uint8_t* flags, cudaStream_t s,
+                            KernelTimer* t) {
     auto fn = k_remove<G, KM>;
+    if (t) t->begin(KK_REMOVE, s);
     fn<<<persistent_grid(fn, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags);
+    if (t) t->end(KK_REMOVE, s);
     return cudaGetLastError();
   }
   static cudaError_t insert_chunk(const DevFilter& d, const uint64_t* keys,
                                   uint32_t n, uint8_t* flags, uint32_t* evout,
-                                  uint32_t* queue, cudaStream_t s) {
+                                  uint32_t* queue, cudaStream_t s,
+                                  KernelTimer* t) {
     auto f1 = k_insert_direct<G, KM>;
+    if (t) t->begin(KK_INSERT_DIRECT, s);
     f1<<<persistent_grid(f1, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags,
                                                              evout, queue);
+    if (t) t->end(KK_INSERT_DIRECT, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto f2 = k_insert_evict<G>;
     const int occ = cached_occupancy(reinterpret_cast<const void*>(f2), kBlock);
+    if (t) t->begin(KK_INSERT_EVICT, s);
     f2<<<unsigned(device_sm_count() * (occ > 0 ? occ : 1)), kBlock, 0, s>>>(
         d, keys, flags, evout, queue);
+    if (t) t->end(KK_INSERT_EVICT, s);
     return cudaGetLastError();
   }
   static cudaError_t insert_serial(const DevFilter& d, const uint64_t* keys,
@@ -619,11 +693,12 @@ struct Launch {
 
 struct Ops {
   cudaError_t (*contains)(const DevFilter&, const uint64_t*, uint64_t,
-                          uint8_t*, cudaStream_t);
+                          uint8_t*, cudaStream_t, KernelTimer*);
   cudaError_t (*remove)(const DevFilter&, const uint64_t*, uint64_t, uint8_t*,
-                        cudaStream_t);
+                        cudaStream_t, KernelTimer*);
   cudaError_t (*insert_chunk)(const DevFilter&, const uint64_t*, uint32_t,
-                              uint8_t*, uint32_t*, uint32_t*, cudaStream_t);
+                              uint8_t*, uint32_t*, uint32_t*, cudaStream_t,
+                              KernelTimer*);
   cudaError_t (*insert_serial)(const DevFilter&, const uint64_t*, uint64_t,
                                uint8_t*, uint32_t*, cudaStream_t);
   cudaError_t (*hash)(const DevFilter&, const uint64_t*, uint64_t, uint32_t*,

@@ -72,7 +72,8 @@ extern "C" cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = cfk::order_on(f, s);
   if (st != CF_OK) return st;
-  e = f->ops->insert_chunk(f->d, keys, uint32_t(n), out_flags, nullptr, queue, s);
+  e = f->ops->insert_chunk(f->d, keys, uint32_t(n), out_flags, nullptr, queue, s,
+                           f->timer);
   if (e != cudaSuccess) {
     cfk::set_error("cf_insert_noalloc launch", e);
     return CF_ECUDA;

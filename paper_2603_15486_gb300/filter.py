@@ -13,8 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (CfBatchItem, CfCompletion, CfConfig, CfRequest, CfServerConfig,
-                   CfServerStats, CfStats, CfTuning, check)
+from ._lib import (KERNEL_KINDS, CfBatchItem, CfCompletion, CfConfig, CfKernelTimes,
+                   CfRequest, CfServerConfig, CfServerStats, CfStats, CfTuning, check)
 
 POLICIES = {"xor": 0, "offset": 1}
 EVICTIONS = {"bfs": 0, "dfs": 1}
@@ -239,6 +239,17 @@ class CuckooFilter:
         check(self._L.cf_count_occupied(self._h, ctypes.byref(v), _stream_handle(stream)),
               "cf_count_occupied")
         return v.value
+
+    def set_kernel_timing(self, enable: bool = True):
+        check(self._L.cf_set_kernel_timing(self._h, int(bool(enable))), "cf_set_kernel_timing")
+
+    def kernel_times(self, reset: bool = True) -> dict:
+        """{kernel: (launches, total ms)} measured with CUDA events on the
+        launching streams while timing was enabled."""
+        t = CfKernelTimes()
+        check(self._L.cf_read_kernel_times(self._h, ctypes.byref(t), int(bool(reset))),
+              "cf_read_kernel_times")
+        return {k: (int(t.launches[i]), float(t.ms[i])) for i, k in enumerate(KERNEL_KINDS)}
 
     def table_view(self) -> torch.Tensor:
         """The live device table as a uint8 tensor (no copy; do not write)."""

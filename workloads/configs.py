@@ -80,7 +80,13 @@ REF_STEP = Workload(name="ref_2^20x4_f16_lf0.95", m=1 << 20, f=16, b=4,
                     max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
                     n_queries=1 << 22, query_pos_seed=12, n_deletes=1 << 20)
 
-BY_NAME = {w.name: w for w in (SINGLE, LARGE, MEDIUM, SCALE, REF_STEP)}
+# The same structure at 2^25 buckets (256 MiB table, twice L2; about 3 GB on
+# the device in all): the size at which kernels are profiled with ncu.
+PROFILE = Workload(name="profile_2^25x4_f16_lf0.95", m=1 << 25, f=16, b=4,
+                   max_evictions=500, key_seed=2, alphas=(0.5, 0.8, 0.95),
+                   n_queries=1 << 27, query_pos_seed=12, n_deletes=1 << 25)
+
+BY_NAME = {w.name: w for w in (SINGLE, LARGE, MEDIUM, SCALE, REF_STEP, PROFILE)}
 
 
 def multi_filter_layout(n_filters: int = 512, e_lo: int = 8, e_hi: int = 22,
