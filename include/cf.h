@@ -416,6 +416,13 @@ cf_status cf_probe_gather(const void* buf, uint64_t bytes, uint64_t n_access,
                           uint32_t access_bytes, uint32_t loads_per_thread,
                           uint64_t seed, unsigned long long* sink,
                           void* stream);
+/* The same random 8-byte loads with a chosen cache operator: flavour 0
+ * ld.global.nc.L1::no_allocate, 1 ld.global.cg, 2 ld.global.cs, 3
+ * ld.global (default), 4 ld.global.lu; 8 loads in flight per thread. */
+cf_status cf_probe_gather_flavour(const void* buf, uint64_t bytes,
+                                  uint64_t n_access, uint32_t flavour,
+                                  uint64_t seed, unsigned long long* sink,
+                                  void* stream);
 /* The CUDA context limit cudaLimitMaxL2FetchGranularity of the current
  * device (0..128 bytes): how much L2 fetches from DRAM around a missed
  * sector.  Random bucket probes use one 32-byte sector; a larger fetch

@@ -129,6 +129,7 @@ SIGNATURES = {
     "cf_set_kernel_timing": (_st, [_vp, _int]),
     "cf_read_kernel_times": (_st, [_vp, ctypes.POINTER(CfKernelTimes), _int]),
     "cf_probe_gather": (_st, [_vp, _u64, _u64, _u32, _u32, _u64, _vp, _vp]),
+    "cf_probe_gather_flavour": (_st, [_vp, _u64, _u64, _u32, _u64, _vp, _vp]),
     "cf_set_l2_fetch_granularity": (_st, [_u32]),
     "cf_get_l2_fetch_granularity": (_st, [ctypes.POINTER(_u32)]),
     "cf_status_str": (ctypes.c_char_p, [_st]),

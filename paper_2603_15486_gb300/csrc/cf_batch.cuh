@@ -35,7 +35,7 @@ struct BatchCtl {
   uint64_t n_tiles;
   unsigned long long next_tile;
   unsigned int queue_count;
-  unsigned int evict_next;  // next eviction-queue entry to hand out
+  unsigned int pad0;
   unsigned long long pad[4];
 };
 static_assert(sizeof(BatchCtl) == 64, "batch header is 64 bytes");
@@ -114,47 +114,44 @@ k_batch_tiles(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
 }
 
 // The combined eviction queue of all inserting items, with the lane
-// refill of k_insert_evict: each warp iteration runs one round of every
-// lane's chain; lanes whose chain ended take the next queued key.
+// refill of k_insert_evict over per-warp shares of the queue.
 template <class G, int FW, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_batch_evict(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
               const uint2* __restrict__ queue) {
   const uint32_t qn = *reinterpret_cast<const volatile unsigned int*>(&ctl->queue_count);
   const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t n_warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t next = uint32_t(uint64_t(qn) * warp / n_warps);
+  const uint32_t end = uint32_t(uint64_t(qn) * (warp + 1) / n_warps);
   Chain<G> c{};
   uint2 q{};
-  bool active = false, dry = false;
+  bool active = false;
   for (;;) {
-    if (!dry) {
+    if (next < end) {
       const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
-      if (need) {
-        const int leader = __ffs(need) - 1;
-        uint32_t base = 0;
-        if (int(lane) == leader) base = atomicAdd(&ctl->evict_next, __popc(need));
-        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (base + __popc(need) >= qn) dry = true;
-        if (!active) {
-          const uint32_t e = base + __popc(need & ((1u << lane) - 1u));
-          if (e < qn) {
-            q = queue[e];
-            const BatchItemDev& I = items[q.x];
-            const DevFilter d = I.d;
-            const KeyHash kh = hash_key<G>(d, I.keys[q.y]);
-            if (d.max_ev == 0) {
-              log_victim(d, kh.fp, kh.i1);
-              if (I.flags) st_flag(I.flags + q.y, EV_FAIL);
-              atomicAdd(&d.ctrl->insert_fail, 1ull);
-            } else {
-              c = chain_start<G>(d, kh);
-              active = true;
-            }
+      if (!active) {
+        const uint32_t e = next + __popc(need & ((1u << lane) - 1u));
+        if (e < end) {
+          q = queue[e];
+          const BatchItemDev& I = items[q.x];
+          const DevFilter d = I.d;
+          const KeyHash kh = hash_key<G>(d, I.keys[q.y]);
+          if (d.max_ev == 0) {
+            log_victim(d, kh.fp, kh.i1);
+            if (I.flags) st_flag(I.flags + q.y, EV_FAIL);
+            atomicAdd(&d.ctrl->insert_fail, 1ull);
+          } else {
+            c = chain_start<G>(d, kh);
+            active = true;
           }
         }
       }
+      next += __popc(need);
     }
     if (!__any_sync(0xFFFFFFFFu, active)) {
-      if (dry) break;
+      if (next >= end) break;
       continue;
     }
     if (active) {

@@ -409,10 +409,11 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
 // Insert, phase 2: the eviction loop for every queued key.  Chains have
 // very different lengths, so a lane does not run one chain to its end:
 // every warp iteration runs ONE round of each lane's chain, and lanes whose
-// chain ended take the next queued key (one atomic per warp).  Warps stay
-// full until the queue runs dry instead of waiting for their longest chain.
-// The queue length is read on the device, so no host round trip separates
-// the two phases; the last block to finish resets the queue.
+// chain ended take the next key of the warp's share of the queue.  Each
+// warp owns a contiguous share (no shared cursor to contend on), and warps
+// stay full until their share runs dry instead of waiting for their
+// longest chain.  The queue length is read on the device, so no host round
+// trip separates the two phases; the last block to finish resets the queue.
 template <class G>
 __global__ void __launch_bounds__(kBlock)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
@@ -420,40 +421,38 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
                const uint32_t* __restrict__ queue) {
   const uint32_t qn = *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
   const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t n_warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t next = uint32_t(uint64_t(qn) * warp / n_warps);
+  const uint32_t end = uint32_t(uint64_t(qn) * (warp + 1) / n_warps);
   uint32_t n_ok = 0, n_fail = 0, n_ev = 0;
   EvictCounters ec;
   Chain<G> c{};
   uint32_t idx = 0;
-  bool active = false, dry = false;
+  bool active = false;
   for (;;) {
-    if (!dry) {
+    if (next < end) {
       const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
-      if (need) {
-        const int leader = __ffs(need) - 1;
-        uint32_t base = 0;
-        if (int(lane) == leader) base = atomicAdd(&d.ctrl->evict_next, __popc(need));
-        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (base + __popc(need) >= qn) dry = true;
-        if (!active) {
-          const uint32_t e = base + __popc(need & ((1u << lane) - 1u));
-          if (e < qn) {
-            idx = queue[e];
-            const KeyHash kh = hash_key<G>(d, keys[idx]);
-            if (d.max_ev == 0) {
-              log_victim(d, kh.fp, kh.i1);
-              if (flags) st_flag(flags + idx, EV_FAIL);
-              if (evout) evout[idx] = 0;
-              n_fail++;
-            } else {
-              c = chain_start<G>(d, kh);
-              active = true;
-            }
+      if (!active) {
+        const uint32_t e = next + __popc(need & ((1u << lane) - 1u));
+        if (e < end) {
+          idx = queue[e];
+          const KeyHash kh = hash_key<G>(d, keys[idx]);
+          if (d.max_ev == 0) {
+            log_victim(d, kh.fp, kh.i1);
+            if (flags) st_flag(flags + idx, EV_FAIL);
+            if (evout) evout[idx] = 0;
+            n_fail++;
+          } else {
+            c = chain_start<G>(d, kh);
+            active = true;
           }
         }
       }
+      next += __popc(need);
     }
     if (!__any_sync(0xFFFFFFFFu, active)) {
-      if (dry) break;
+      if (next >= end) break;
       continue;
     }
     if (active) {
@@ -483,7 +482,6 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
     const unsigned prev = atomicAdd(&d.ctrl->done_blocks, 1u);
     if (prev == gridDim.x - 1) {
       d.ctrl->queue_count = 0;
-      d.ctrl->evict_next = 0;
       d.ctrl->done_blocks = 0;
       __threadfence();
     }

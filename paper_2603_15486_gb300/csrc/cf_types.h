@@ -21,7 +21,7 @@ struct Ctrl {
   unsigned int error_word;
   unsigned int queue_count;  // eviction work queue fill (insert scratch)
   unsigned int done_blocks;  // last-block-done counter of the evict kernel
-  unsigned int evict_next;   // next eviction-queue entry to hand out
+  unsigned int pad0;
   unsigned long long scratch_count;  // for cf_count_occupied
   unsigned long long pad[19];
 };
