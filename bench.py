@@ -821,16 +821,66 @@ def ablation_arm(args):
             "eviction": evict, "bucket_policy": policy}
 
 
+# ---------------------------------------------------------------------------
+# Probe mode: the random-access ceiling of this GPU's HBM.
+# ---------------------------------------------------------------------------
+FLAVOURS = ["ld.global.nc.L1::no_allocate", "ld.global.cg", "ld.global.cs", "ld.global",
+            "ld.global.lu", "ld.relaxed.gpu.global", "ld.volatile.global",
+            "ld.global.nc.L1::no_allocate.L2::64B", "ld.global.nc.L1::no_allocate.L2::256B",
+            "atom.global.or.b64 (0)"]
+
+
+def probe_arm(args):
+    import torch
+    from paper_2603_15486_gb300 import _lib
+
+    torch.cuda.set_device(0)
+    L = _lib.load()
+    st = torch.cuda.Stream()
+    sh = st.cuda_stream
+    n = args.probe_n
+    buf = torch.zeros(1 << 31, dtype=torch.uint8, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def timed(launch):
+        for _ in range(2):
+            assert launch(7) == 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        launch(9)
+        e1.record(st)
+        st.synchronize()
+        return round(n / e0.elapsed_time(e1) / 1e6, 2)
+
+    by_flavour = {FLAVOURS[fl]: timed(lambda seed, fl=fl: L.cf_probe_gather_flavour(
+        buf.data_ptr(), buf.numel(), n, fl, seed, sink.data_ptr(), sh)) for fl in range(10)}
+    by_shape = {}
+    for ab in (8, 32):
+        for lp in (4, 8, 16):
+            by_shape[f"{ab}B_x{lp}"] = timed(lambda seed, ab=ab, lp=lp: L.cf_probe_gather(
+                buf.data_ptr(), buf.numel(), n, ab, lp, seed, sink.data_ptr(), sh))
+    l2 = timed(lambda seed: L.cf_probe_gather(buf.data_ptr(), 1 << 26, n, 8, 8, seed,
+                                              sink.data_ptr(), sh))
+    return {"metric": "random load rate (G loads/s) over a 2 GiB buffer", "mode": "probe",
+            "unit": "G loads/s", "value": by_flavour[FLAVOURS[0]], "n_gpus": 1,
+            "higher_is_better": True, "config": {"loads": n, "buffer_bytes": 1 << 31},
+            "by_load_form": by_flavour, "by_size_and_loads_in_flight": by_shape,
+            "l2_resident_64MiB_8B_x8": l2}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation"], default="main",
+    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation", "probe"],
+                    default="main",
                     help="main: the large-filter headline; batched / serve: the "
                          "many-filters and serving workloads (one JSON line each)")
     ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--probe-n", type=int, default=1 << 30)
     ap.add_argument("--workload", default="large_2^28x4_f16_lf0.95")
     ap.add_argument("--cpu-workload", default="scale_2^22x4_f16_lf0.95")
     ap.add_argument("--ref-workload", default="ref_2^20x4_f16_lf0.95")
@@ -851,6 +901,8 @@ def main(argv=None):
         out = serve_arm(args)
     elif args.mode == "ablation":
         out = ablation_arm(args)
+    elif args.mode == "probe":
+        out = probe_arm(args)
     else:
         out = gpu_arm(args)
     if out is not None:

@@ -416,9 +416,12 @@ cf_status cf_probe_gather(const void* buf, uint64_t bytes, uint64_t n_access,
                           uint32_t access_bytes, uint32_t loads_per_thread,
                           uint64_t seed, unsigned long long* sink,
                           void* stream);
-/* The same random 8-byte loads with a chosen cache operator: flavour 0
+/* The same random 8-byte loads with a chosen load form: flavour 0
  * ld.global.nc.L1::no_allocate, 1 ld.global.cg, 2 ld.global.cs, 3
- * ld.global (default), 4 ld.global.lu; 8 loads in flight per thread. */
+ * ld.global (default), 4 ld.global.lu, 5 ld.relaxed.gpu.global, 6
+ * ld.volatile.global, 7 flavour 0 with the .L2::64B prefetch-size hint, 8
+ * with .L2::256B, 9 atom.global.or.b64 with 0 (a read performed at L2);
+ * 8 loads in flight per thread.  The buffer is not modified. */
 cf_status cf_probe_gather_flavour(const void* buf, uint64_t bytes,
                                   uint64_t n_access, uint32_t flavour,
                                   uint64_t seed, unsigned long long* sink,

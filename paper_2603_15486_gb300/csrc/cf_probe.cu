@@ -36,13 +36,23 @@ __device__ __forceinline__ unsigned long long ld_flavour(const unsigned long lon
     asm volatile("ld.global.cs.u64 %0, [%1];" : "=l"(v) : "l"(p));
   else if constexpr (FL == 3)
     asm volatile("ld.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else
+  else if constexpr (FL == 4)
     asm volatile("ld.global.lu.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  else if constexpr (FL == 5)
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  else if constexpr (FL == 6)
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  else if constexpr (FL == 7)
+    asm volatile("ld.global.nc.L1::no_allocate.L2::64B.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  else if constexpr (FL == 8)
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  else
+    asm volatile("atom.global.or.b64 %0, [%1], 0;" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-// 8-byte random loads with flavour FL (0 nc+L1::no_allocate, 1 cg, 2 cs,
-// 3 default, 4 lu), KP in flight per thread.
+// 8-byte random loads with flavour FL (see cf_probe_gather_flavour), KP in
+// flight per thread.
 template <int FL, int KP>
 __global__ void __launch_bounds__(kProbeBlock)
 k_gather_flavour(const unsigned long long* __restrict__ buf, uint64_t n_slots,
@@ -143,7 +153,7 @@ cf_status cf_probe_gather_flavour(const void* buf, uint64_t bytes,
                                   uint64_t n_access, uint32_t flavour,
                                   uint64_t seed, unsigned long long* sink,
                                   void* stream) {
-  if (!buf || !sink || flavour > 4) return CF_EINVAL;
+  if (!buf || !sink || flavour > 9) return CF_EINVAL;
   if ((reinterpret_cast<uintptr_t>(buf) & 31) != 0) return CF_EINVAL;
   uint64_t slots = bytes / 8;
   if (slots == 0 || n_access == 0) return CF_EINVAL;
@@ -156,7 +166,12 @@ cf_status cf_probe_gather_flavour(const void* buf, uint64_t bytes,
     case 1: e = launch_flavour<1>(p, slots, n_access, seed, sink, s); break;
     case 2: e = launch_flavour<2>(p, slots, n_access, seed, sink, s); break;
     case 3: e = launch_flavour<3>(p, slots, n_access, seed, sink, s); break;
-    default: e = launch_flavour<4>(p, slots, n_access, seed, sink, s); break;
+    case 4: e = launch_flavour<4>(p, slots, n_access, seed, sink, s); break;
+    case 5: e = launch_flavour<5>(p, slots, n_access, seed, sink, s); break;
+    case 6: e = launch_flavour<6>(p, slots, n_access, seed, sink, s); break;
+    case 7: e = launch_flavour<7>(p, slots, n_access, seed, sink, s); break;
+    case 8: e = launch_flavour<8>(p, slots, n_access, seed, sink, s); break;
+    default: e = launch_flavour<9>(p, slots, n_access, seed, sink, s); break;
   }
   return e == cudaSuccess ? CF_OK : CF_ECUDA;
 }
