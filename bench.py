@@ -195,6 +195,31 @@ def kernel_bytes(phases: dict, bucket_bytes: int, n_insert: int, n_query: int,
             "remove": n_delete * ((d["bucket_reads"] + d["bucket_writes"]) / d["ops"] * spb + 9)}
 
 
+def slice_kernel_bytes(phases: dict, W, chunk: int) -> dict:
+    """Bytes the slice-partitioned passes must move per step (their streams,
+    plus one sweep of the table per bucket pass: read, and written back for
+    insert / delete), from the workload's operation counts and the oracle's
+    fraction of keys that need their second bucket."""
+    tb = W.table_bytes
+    calls = {"insert": [hi - lo for lo, hi in W.insert_segments()],
+             "query": [W.n_queries], "delete": [W.n_deletes]}
+    ins, q, d = phases["insert"], phases["query"], phases["delete"]
+    pend = {"insert": ins["direct_reads"] / ins["ops"] - 1.0,
+            "query": q["bucket_reads"] / q["ops"] - 1.0,
+            "delete": d["bucket_reads"] / d["ops"] - 1.0}
+    out = {"slice_split": 0.0, "slice_probe1": 0.0, "slice_probe2": 0.0, "slice_merge": 0.0}
+    for op, sizes in calls.items():
+        n = sum(sizes)
+        passes = sum(math.ceil(x / chunk) for x in sizes)
+        sweep = tb * (1 if op == "query" else 2) * passes
+        pf = max(0.0, pend[op])
+        out["slice_split"] += n * (8 + 8 + 8 + 4)
+        out["slice_probe1"] += n * (8 + 1 + pf * (8 + 4)) + sweep
+        out["slice_probe2"] += n * pf * (8 + 1) + sweep
+        out["slice_merge"] += n * (2 + pf * (4 + 1) + 4 + 1 + 1)
+    return out
+
+
 def bytes_per_op(phases: dict, bucket_bytes: int) -> dict:
     """Algorithmic bytes per operation: the 32-byte sectors of the buckets
     the algorithm reads and writes (counted by the oracle), plus the 8-byte
@@ -243,6 +268,7 @@ def gpu_arm(args):
     q_flags = torch.empty(W.n_queries, dtype=torch.uint8, device=dev)
     d_flags = torch.empty(W.n_deletes, dtype=torch.uint8, device=dev)
     filt = CuckooFilter(W.m, W.f, W.b, W.max_evictions)
+    filt.set_slicing(args.slicing, 0, args.slice_chunk)
     stream.synchronize()
 
     segs = W.insert_segments()
@@ -332,6 +358,7 @@ def gpu_arm(args):
                    "deletes": W.n_deletes, "table_bytes": W.table_bytes,
                    "keys": "splitmix64 seed 2, uniform uint64",
                    "parallelism": f"replicas x{ws}",
+                   "slicing": args.slicing, "slice_chunk": args.slice_chunk or (1 << 28),
                    "l2": "no flush: 2 GiB table and 8 GB key arrays exceed the 129 MB L2"},
         "phases": {k: {"ms": round(v * 1e3, 3),
                        "mops": round(n / v / 1e6, 1)}
@@ -362,6 +389,7 @@ def gpu_arm(args):
                           "one thread of the host)"),
                "phases_mops": {k: round(p["ops"] / p["s"] / 1e6, 3) for k, p in phases.items()}}
     kb = kernel_bytes(phases, W.f * W.b // 8, W.n_insert, W.n_queries, W.n_deletes)
+    kb.update(slice_kernel_bytes(phases, W, args.slice_chunk or (1 << 28)))
     peak = peaks.get("hbm_gbs") or 6800.0
     kern = {}
     for k, (launches, ms) in ktimes.items():
@@ -370,8 +398,17 @@ def gpu_arm(args):
         ach = kb[k] * args.steps / (ms / 1e3) / 1e9
         kern[k] = {"launches": launches, "avg_launch_ms": round(ms / launches, 4),
                    "total_ms_per_step": round(ms / args.steps, 3),
-                   "algorithmic_bytes_per_step": int(kb[k]),
+                   ("stream_bytes_per_step" if k.startswith("slice") else
+                    "algorithmic_bytes_per_step"): int(kb[k]),
                    "achieved_GBps": round(ach, 1), "frac": round(ach / peak, 4)}
+    # Per operation: the method's algorithmic bytes (32 B per bucket sector
+    # the oracle touches + 9 B) at the measured operation rate.
+    bpo = bytes_per_op(phases, W.f * W.b // 8)
+    for name, key in (("insert", "insert"), ("query", "query"), ("delete", "delete")):
+        ph = out["phases"][name]
+        gbps = ph["mops"] * 1e6 * bpo[key] / 1e9
+        ph.update({"algorithmic_bytes_per_op": round(bpo[key], 1),
+                   "achieved_GBps": round(gbps, 1), "frac": round(gbps / peak, 4)})
     dom = max(kern, key=lambda k: kern[k]["total_ms_per_step"])
     ceiling = random_gather_ceiling(stream)
     out["roofline"] = {"bound": "hbm", "kernel": dom,
@@ -888,6 +925,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-warmup", type=int, default=1)
+    ap.add_argument("--slicing", choices=["off", "auto", "always"], default="auto",
+                    help="slice-partitioned execution of the filter calls (cf_set_slicing)")
+    ap.add_argument("--slice-chunk", type=int, default=0,
+                    help="keys per sliced pass (0: the library default, 2^28)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args(argv)

@@ -169,6 +169,35 @@ cf_status cf_remove_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
 /* Keys per staging chunk for the *_host calls (default 2^24). */
 cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk);
 
+/* Slice-partitioned execution of cf_insert / cf_contains / cf_remove (and of
+ * each staging chunk of the *_host calls).  The paper's kernels have no
+ * counterpart: they give every key one thread and let it touch its buckets in
+ * batch order.  Here a batch is grouped by the table slice of each key's
+ * primary bucket and processed slice by slice, so that bucket accesses hit
+ * L2; keys left pending (not found / not removed / bucket full) are grouped
+ * by the slice of their alternate bucket and processed again; the insert's
+ * eviction loop (Sec. 4.6.1) then runs on the keys whose two buckets were
+ * full.  Each key follows Alg. 1 / 2 / 3 exactly as on the plain path; only
+ * the interleaving of keys differs, so query flags are identical and insert
+ * / delete results satisfy the same invariants (which keys win a contended
+ * bucket may differ, as between any two concurrent runs).
+ *  - mode: 0 never, 1 automatic (the default: tables of at least 512 MiB and
+ *    batches of at least num_buckets / 8 keys), 2 always.
+ *  - slice_bytes: table bytes per slice, rounded down to a power-of-two
+ *    number of buckets (0: 16 MiB).  At most 1024 slices: larger tables get
+ *    larger slices.  CF_EINVAL if smaller than one bucket.
+ *  - max_chunk: keys per sliced pass (0: 2^28, at most 2^30, CF_EINVAL
+ *    above).  Larger batches run as consecutive passes.
+ *  - Scratch: about 36 bytes per key of a pass (its largest pass so far),
+ *    allocated by the library on the first sliced call and freed by
+ *    cf_destroy or by a change of slice_bytes / max_chunk.  CF_ENOMEM if it
+ *    cannot be allocated.
+ *  - Calls that ask for per-key eviction counts (cf_insert_ex with
+ *    out_evictions) take the plain path.
+ * Waits for the filter's queued work before changing the settings. */
+cf_status cf_set_slicing(cf_filter* f, int mode, uint64_t slice_bytes,
+                         uint64_t max_chunk);
+
 /* ---- state, stats, snapshots (synchronous) ------------------------------ */
 cf_status cf_stats(cf_filter* f, cf_stats_t* out, void* stream);
 /* Copy the first min(max, logged) victims (tag, bucket) to host arrays;
@@ -395,13 +424,17 @@ cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
 /* ---- measurement helpers ------------------------------------------------ */
 /* Per-kernel device time of one filter's single-filter calls: while enabled,
  * an event pair is recorded on the launching stream around every kernel
- * launch.  Index 0: insert phase 1 (direct insertion into i1 / i2), 1:
- * insert phase 2 (eviction loop), 2: contains, 3: remove.
+ * launch (around each group of launches for the sliced passes).  Index 0:
+ * insert phase 1 (direct insertion into i1 / i2), 1: insert phase 2
+ * (eviction loop, both paths), 2: contains, 3: remove; slice-partitioned
+ * path (cf_set_slicing): 4: grouping by slice (histogram, prefix, scatter),
+ * 5: bucket-i1 pass, 6: bucket-i2 pass, 7: results back to key order.
  * cf_read_kernel_times waits for the recorded events, sums their elapsed
  * times and (reset != 0) recycles them. */
+#define CF_KERNEL_KINDS 8
 typedef struct {
-  uint64_t launches[4];
-  double ms[4];
+  uint64_t launches[CF_KERNEL_KINDS];
+  double ms[CF_KERNEL_KINDS];
 } cf_kernel_times;
 cf_status cf_set_kernel_timing(cf_filter* f, int enable);
 cf_status cf_read_kernel_times(cf_filter* f, cf_kernel_times* out, int reset);

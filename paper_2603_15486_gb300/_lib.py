@@ -64,11 +64,13 @@ class CfServerStats(ctypes.Structure):
         ("live_filters", ctypes.c_uint32), ("pending_filters", ctypes.c_uint32)]
 
 
+KERNEL_KINDS = ("insert_direct", "insert_evict", "contains", "remove",
+                "slice_split", "slice_probe1", "slice_probe2", "slice_merge")
+
+
 class CfKernelTimes(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 4), ("ms", ctypes.c_double * 4)]
-
-
-KERNEL_KINDS = ("insert_direct", "insert_evict", "contains", "remove")
+    _fields_ = [("launches", ctypes.c_uint64 * len(KERNEL_KINDS)),
+                ("ms", ctypes.c_double * len(KERNEL_KINDS))]
 
 
 # Every symbol include/cf.h declares, with (restype, argtypes).
@@ -94,6 +96,7 @@ SIGNATURES = {
     "cf_contains_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
     "cf_remove_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
     "cf_set_staging_chunk": (_st, [_vp, _u64]),
+    "cf_set_slicing": (_st, [_vp, _int, _u64, _u64]),
     "cf_stats": (_st, [_vp, ctypes.POINTER(CfStats), _vp]),
     "cf_victims": (_st, [_vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "cf_snapshot": (_st, [_vp, _vp, ctypes.c_size_t, _int, _vp]),

@@ -3,10 +3,12 @@
 // One filter = one device allocation laid out as
 //   [control block 256 B][victim log, 16 B per entry][table]
 // (each piece 256-byte aligned), plus library-owned scratch: the eviction
-// work queue of the insert (4 bytes per key of the largest chunk seen) and,
-// for the *_host calls, two staging slots of keys and flags.
+// work queue of the insert (4 bytes per key of the largest chunk seen), the
+// scratch of the slice-partitioned path (about 36 bytes per key of its chunk)
+// and, for the *_host calls, two staging slots of keys and flags.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -25,6 +27,13 @@ using cfk::Stage;
 namespace {
 
 constexpr uint64_t kInsertChunk = 1ull << 28;  // keys per insert launch pair
+// Slice-partitioned path: defaults and the automatic rule.  A slice of 16 MiB
+// stays resident in L2 (129 MB) next to the streams; the path pays off when
+// the table is several times L2 and a batch touches each slice many times.
+constexpr uint64_t kSliceBytes = 16ull << 20;
+constexpr uint64_t kSliceChunk = 1ull << 28;   // keys per sliced pass
+constexpr uint64_t kSliceChunkMax = 1ull << 30;
+constexpr uint64_t kSliceAutoTable = 512ull << 20;
 constexpr uint32_t kDefaultVictims = 4096;
 constexpr uint32_t kMaxVictims = 1u << 26;
 
@@ -177,8 +186,8 @@ namespace {
 using cfk::mark;
 using cfk::order_on;
 
-cf_status ensure_queue(cf_filter* f, uint64_t keys) {
-  const uint64_t want = keys < kInsertChunk ? keys : kInsertChunk;
+cf_status ensure_queue(cf_filter* f, uint64_t keys, uint64_t cap = kInsertChunk) {
+  const uint64_t want = keys < cap ? keys : cap;
   if (want <= f->queue_cap) return CF_OK;
   if (f->queue) CF_CUDA(cudaFree(f->queue));
   f->queue = nullptr;
@@ -246,10 +255,109 @@ cf_status ensure_staging(cf_filter* f) {
   return CF_OK;
 }
 
-enum Op { OP_INSERT, OP_CONTAINS, OP_REMOVE };
+enum Op { OP_INSERT, OP_CONTAINS, OP_REMOVE };  // = cfk::SOP_* values
+
+// Slice geometry of a filter: 2^shift buckets per slice, S slices, S at most
+// kSliceMax (larger tables get larger slices).
+void slice_geometry(const cf_filter* f, uint32_t* shift, uint32_t* S) {
+  const uint64_t bb = uint64_t(f->cfg.slots_per_bucket) * f->cfg.fp_bits / 8;
+  const uint64_t want = (f->slice_bytes ? f->slice_bytes : kSliceBytes) / bb;
+  uint32_t sh = 0;
+  while ((2ull << sh) <= want) ++sh;
+  const uint64_t m = f->cfg.num_buckets;
+  while (((m + (1ull << sh) - 1) >> sh) > cfk::kSliceMax) ++sh;
+  *shift = sh;
+  *S = uint32_t((m + (1ull << sh) - 1) >> sh);
+}
+
+uint64_t slice_chunk(const cf_filter* f) {
+  return f->slice_chunk ? f->slice_chunk : kSliceChunk;
+}
+
+bool use_sliced(const cf_filter* f, uint64_t n, const uint32_t* evout) {
+  if (evout || f->slice_mode == 0) return false;
+  if (f->slice_mode == 2) return true;
+  return table_bytes(&f->cfg) >= kSliceAutoTable && n >= f->cfg.num_buckets / 8;
+}
+
+void free_slice(cf_filter* f) {
+  if (f->sb_mem) cudaFree(f->sb_mem);
+  f->sb_mem = nullptr;
+  f->sb = cfk::SliceBufs{};
+  f->sb_cap = 0;
+}
+
+// Scratch for chunks of up to n keys (one allocation, 256-byte aligned
+// pieces).  rec2 holds S regions of cap2 records plus a spill region of n:
+// cap2 = n/S + 6 sqrt(n/S) + 64 keeps uniform hashes inside their slice.
+cf_status ensure_slice(cf_filter* f, uint64_t n) {
+  uint32_t shift = 0, S = 0;
+  slice_geometry(f, &shift, &S);
+  if (f->sb_mem && f->sb_cap >= n && f->sb.n_slices == S && f->sb.shift == shift)
+    return CF_OK;
+  free_slice(f);
+  const double per = double(n) / S;
+  const uint64_t cap2 = uint64_t(per + 6.0 * sqrt(per)) + 64;
+  const uint64_t n2 = uint64_t(S) * cap2 + n;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  // Counters one per 128-byte line (32 words apart).
+  const size_t o_cursor = take(size_t(S) * 128), o_fill2 = take(size_t(S + 1) * 128);
+  const size_t o_dst = take(n * 4), o_rec1 = take(n * 8), o_f1 = take(n);
+  const size_t o_link = take(n * 4), o_rec2 = take(n2 * 8), o_f2 = take(n2);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_err, sizeof g_err, "slice scratch of %llu bytes", (unsigned long long)off);
+    return CF_ENOMEM;
+  }
+  cfk::SliceBufs& b = f->sb;
+  b.n_slices = S;
+  b.shift = shift;
+  b.cap2 = cap2;
+  b.cursor = reinterpret_cast<uint32_t*>(mem + o_cursor);
+  b.fill2 = reinterpret_cast<uint32_t*>(mem + o_fill2);
+  b.dst = reinterpret_cast<uint32_t*>(mem + o_dst);
+  b.rec1 = reinterpret_cast<uint64_t*>(mem + o_rec1);
+  b.f1 = reinterpret_cast<uint8_t*>(mem + o_f1);
+  b.link = reinterpret_cast<uint32_t*>(mem + o_link);
+  b.rec2 = reinterpret_cast<uint64_t*>(mem + o_rec2);
+  b.f2 = reinterpret_cast<uint8_t*>(mem + o_f2);
+  f->sb_mem = mem;
+  f->sb_cap = n;
+  return CF_OK;
+}
+
+cf_status run_sliced(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
+                     uint8_t* flags, cudaStream_t s) {
+  const uint64_t chunk = slice_chunk(f);
+  const uint64_t first = n < chunk ? n : chunk;
+  cf_status st = ensure_slice(f, first);
+  if (st != CF_OK) return st;
+  if (op == OP_INSERT) {
+    st = ensure_queue(f, first, kSliceChunkMax);
+    if (st != CF_OK) return st;
+  }
+  for (uint64_t off = 0; off < n; off += chunk) {
+    const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
+    const cudaError_t e = f->ops->sliced(f->d, int(op), keys + off, len,
+                                         flags ? flags + off : nullptr, f->sb,
+                                         f->queue, s, f->timer);
+    if (e != cudaSuccess) {
+      set_err("sliced kernel launch", e);
+      return CF_ECUDA;
+    }
+  }
+  return CF_OK;
+}
 
 cf_status run_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
                  uint8_t* flags, uint32_t* evout, cudaStream_t s) {
+  if (use_sliced(f, n, evout)) return run_sliced(f, op, keys, n, flags, s);
   cudaError_t e = cudaSuccess;
   if (op == OP_CONTAINS) {
     e = f->ops->contains(f->d, keys, n, flags, s, f->timer);
@@ -362,7 +470,7 @@ cf_status cf_read_kernel_times(cf_filter* f, cf_kernel_times* out, int reset) {
     CF_CUDA(cudaEventSynchronize(r.b));
     float ms = 0.f;
     CF_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
-    if (r.kind >= 0 && r.kind < 4) {
+    if (r.kind >= 0 && r.kind < cfk::KK_NUM) {
       out->launches[r.kind] += 1;
       out->ms[r.kind] += ms;
     }
@@ -374,6 +482,21 @@ cf_status cf_read_kernel_times(cf_filter* f, cf_kernel_times* out, int reset) {
     }
     f->timer->recs.clear();
   }
+  return CF_OK;
+}
+
+cf_status cf_set_slicing(cf_filter* f, int mode, uint64_t slice_bytes,
+                         uint64_t max_chunk) {
+  if (!f || mode < 0 || mode > 2) return CF_EINVAL;
+  const uint64_t bb = uint64_t(f->cfg.slots_per_bucket) * f->cfg.fp_bits / 8;
+  if (slice_bytes && slice_bytes < bb) return CF_EINVAL;
+  if (max_chunk > kSliceChunkMax) return CF_EINVAL;
+  // Scratch in use by queued work is freed only after that work.
+  if (f->has_last) CF_CUDA(cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev));
+  f->slice_mode = mode;
+  if (slice_bytes != f->slice_bytes || max_chunk != f->slice_chunk) free_slice(f);
+  f->slice_bytes = slice_bytes;
+  f->slice_chunk = max_chunk;
   return CF_OK;
 }
 
@@ -462,6 +585,7 @@ cf_status cf_destroy(cf_filter* f) {
   if (f->has_last) cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev);
   free_staging(f);
   if (f->queue) cudaFree(f->queue);
+  free_slice(f);
   if (f->last_ev) cudaEventDestroy(f->last_ev);
   delete f->timer;
   if (f->owns && f->mem) cudaFree(f->mem);

@@ -278,10 +278,9 @@ __device__ __forceinline__ uint32_t alt_index(const DevFilter& d, uint32_t i1,
 // the hash give the fingerprint (0 is EMPTY, so 0 becomes 1), the lower 32
 // bits the primary bucket.
 template <class G>
-__device__ __forceinline__ KeyHash hash_primary(const DevFilter& d,
-                                                uint64_t key) {
+__device__ __forceinline__ KeyHash hash_from_h(const DevFilter& d, uint64_t h) {
   KeyHash k;
-  k.h = xxh64_u64(key);
+  k.h = h;
   const uint32_t raw = uint32_t(k.h >> 32) & G::kFpMask;
   k.fp = raw ? raw : 1u;
   if constexpr (G::POLICY == 0)
@@ -293,8 +292,22 @@ __device__ __forceinline__ KeyHash hash_primary(const DevFilter& d,
 }
 
 template <class G>
+__device__ __forceinline__ KeyHash hash_primary(const DevFilter& d,
+                                                uint64_t key) {
+  return hash_from_h<G>(d, xxh64_u64(key));
+}
+
+template <class G>
 __device__ __forceinline__ KeyHash hash_key(const DevFilter& d, uint64_t key) {
   KeyHash k = hash_primary<G>(d, key);
+  k.i2 = alt_index<G>(d, k.i1, k.fp);
+  return k;
+}
+
+// The full hash record of a key from its 64-bit hash alone.
+template <class G>
+__device__ __forceinline__ KeyHash hash_full_from_h(const DevFilter& d, uint64_t h) {
+  KeyHash k = hash_from_h<G>(d, h);
   k.i2 = alt_index<G>(d, k.i1, k.fp);
   return k;
 }

@@ -94,5 +94,12 @@ struct cf_filter {
   cudaStream_t s_in = nullptr, s_out = nullptr;
   bool stage_ready = false;
   cfk::FilterTimer* timer = nullptr;  // non-null while kernel timing is on
+  // Slice-partitioned path (cf_set_slicing): mode, geometry, scratch.
+  int slice_mode = 1;                  // 0 off, 1 auto, 2 always
+  uint64_t slice_bytes = 0;            // table bytes per slice (0: default)
+  uint64_t slice_chunk = 0;            // keys per sliced pass (0: default)
+  cfk::SliceBufs sb{};
+  uint64_t sb_cap = 0;                 // keys the scratch is sized for
+  void* sb_mem = nullptr;
 };
 

@@ -107,14 +107,10 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
 }
 
 template <class G, int K, bool INSERT>
-__device__ __forceinline__ void cas_many(const DevFilter& d,
-                                         const uint32_t (&bkt)[K],
-                                         const uint32_t (&tag)[K],
-                                         const bool (&act)[K], int (&res)[K]) {
-  if constexpr (G::kWpb == 1) {
-    cas_many_1w<G, K, INSERT>(d, bkt, tag, act, res);
-    return;
-  }
+__device__ __forceinline__ void cas_many_nw(const DevFilter& d,
+                                            const uint32_t (&bkt)[K],
+                                            const uint32_t (&tag)[K],
+                                            const bool (&act)[K], int (&res)[K]) {
   using W = typename G::Word;
   Bucket<G> bk[K];
   W cur[K];
@@ -192,6 +188,17 @@ __device__ __forceinline__ void cas_many(const DevFilter& d,
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (live[k]) res[k] = TI_CONTENTION;
+}
+
+template <class G, int K, bool INSERT>
+__device__ __forceinline__ void cas_many(const DevFilter& d,
+                                         const uint32_t (&bkt)[K],
+                                         const uint32_t (&tag)[K],
+                                         const bool (&act)[K], int (&res)[K]) {
+  if constexpr (G::kWpb == 1)
+    cas_many_1w<G, K, INSERT>(d, bkt, tag, act, res);
+  else
+    cas_many_nw<G, K, INSERT>(d, bkt, tag, act, res);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,7 +421,9 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
 // stay full until their share runs dry instead of waiting for their
 // longest chain.  The queue length is read on the device, so no host round
 // trip separates the two phases; the last block to finish resets the queue.
-template <class G>
+// FROM_HASH: keys[] holds the keys' 64-bit hashes instead of the keys (the
+// slice-partitioned path queues positions of its hash records).
+template <class G, bool FROM_HASH = false>
 __global__ void __launch_bounds__(kBlock)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
                uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
@@ -437,7 +446,8 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
         const uint32_t e = next + __popc(need & ((1u << lane) - 1u));
         if (e < end) {
           idx = queue[e];
-          const KeyHash kh = hash_key<G>(d, keys[idx]);
+          const KeyHash kh = FROM_HASH ? hash_full_from_h<G>(d, keys[idx])
+                                       : hash_key<G>(d, keys[idx]);
           if (d.max_ev == 0) {
             log_victim(d, kh.fp, kh.i1);
             if (flags) st_flag(flags + idx, EV_FAIL);
@@ -618,7 +628,11 @@ enum KernelKind : int {
   KK_INSERT_EVICT = 1,
   KK_CONTAINS = 2,
   KK_REMOVE = 3,
-  KK_NUM = 4
+  KK_SLICE_SPLIT = 4,   // slice-partitioned path: hist + scan + scatter
+  KK_SLICE_PROBE1 = 5,  // ... bucket i1 pass
+  KK_SLICE_PROBE2 = 6,  // ... bucket i2 pass
+  KK_SLICE_MERGE = 7,   // ... merge + out (results back to key order)
+  KK_NUM = 8
 };
 struct KernelTimer {
   virtual void begin(int kind, cudaStream_t s) = 0;
@@ -702,15 +716,13 @@ struct Ops {
   cudaError_t (*hash)(const DevFilter&, const uint64_t*, uint64_t, uint32_t*,
                       uint64_t*, uint64_t*, cudaStream_t);
   cudaError_t (*count)(const DevFilter&, unsigned long long*, cudaStream_t);
+  // Slice-partitioned insert / contains / remove of one chunk (op: 0 / 1 / 2).
+  cudaError_t (*sliced)(const DevFilter&, int, const uint64_t*, uint64_t,
+                        uint8_t*, const SliceBufs&, uint32_t*, cudaStream_t,
+                        KernelTimer*);
 };
 
-template <class G>
-const Ops* ops_for() {
-  static const Ops o = {&Launch<G>::contains, &Launch<G>::remove,
-                        &Launch<G>::insert_chunk, &Launch<G>::insert_serial,
-                        &Launch<G>::hash, &Launch<G>::count};
-  return &o;
-}
+// ops_for<G>() (the table of one geometry) is defined in cf_slice.cuh.
 
 // One per translation unit (fingerprint width).
 const Ops* ops_f8(int b, int policy);

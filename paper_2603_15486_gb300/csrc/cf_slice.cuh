@@ -1,0 +1,632 @@
+// Slice-partitioned execution of query (Alg. 2), delete (Alg. 3) and the
+// direct phase of the insert (Alg. 1), for tables much larger than L2.
+//
+// A random bucket access to a table far larger than L2 costs one DRAM round
+// trip that delivers about four 32-byte sectors, and the plain kernels are
+// bound by the rate of those round trips.  Here a batch is first grouped by
+// the slice of its primary bucket (a slice = 2^shift consecutive buckets,
+// sized to a fraction of L2), and the grouped records are then processed in
+// order: all warps work inside one or two slices at a time, so a slice's
+// buckets come from DRAM about once and every further access hits L2.
+// Records left pending by their primary bucket (not found, not removed, or
+// the bucket was full) are grouped again by the slice of their alternate
+// bucket and processed the same way.  Results go back to the caller's key
+// order through the two permutations; both are made of runs (one per block
+// tile and slice), which keeps those gathers local.
+//
+// Bucket loads here use ld.global.cg (cached in L2 at normal priority): the
+// non-coherent .nc form of the plain query kernel left the slice's lines
+// to be evicted by the streams and re-fetched from DRAM.
+//
+// Every key still runs Alg. 1 / 2 / 3 on its own: bucket i1 first, bucket i2
+// only if i1 did not settle it, the eviction loop only if both were full.
+// Only the interleaving between keys changes, which the concurrent kernels
+// leave open anyway.
+//
+// Passes over a chunk of n keys, S slices:
+//   hist     keys -> per-slice counts of i1's slice
+//   scan     exclusive prefix of the counts -> scatter cursors
+//   scatter  keys -> rec1 (the 64-bit hash of each key, grouped by slice),
+//            dst[j] = rec1 position of key j
+//   probe1   rec1 in order: the operation on bucket i1; pending records ->
+//            rec2 (grouped by i2's slice, cap2 records per slice, overflow in
+//            a spill region after the slices), link[p] = rec2 position
+//   probe2   rec2 in order: the operation on bucket i2; an insert whose two
+//            buckets are full joins the eviction queue (by rec2 position)
+//   evict    (insert) the eviction loop on the queued rec2 records
+//   merge    f1[p] = f2[link[p]] wherever f1[p] is pending
+//   out      flags[j] = f1[dst[j]]
+// Without a flags array the passes that only carry results (dst, f1, link,
+// f2, merge, out) are skipped.
+#pragma once
+
+#include "cf_kernels.cuh"
+
+namespace cfk {
+
+constexpr uint8_t kPending = 0xFF;
+// Per-slice counters are spread one per 128-byte line (kCtrStride words
+// apart): every block tile bumps one counter per slice, and counters packed
+// into a few lines would serialise those atomics on a few L2 slices.
+constexpr uint32_t kCtrStride = 32;
+
+enum : int { SOP_INSERT = 0, SOP_CONTAINS = 1, SOP_REMOVE = 2 };
+
+__device__ __forceinline__ void st_cs_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v));
+}
+__device__ __forceinline__ uint32_t ld_cs_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// hist: counts of i1's slice.  Each block bins its keys in shared memory and
+// adds its bins to the global histogram once.
+// ---------------------------------------------------------------------------
+template <class G, int U>
+__global__ void __launch_bounds__(kBlock)
+k_slice_hist(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
+             uint32_t shift, uint32_t S, uint32_t* __restrict__ hist) {
+  extern __shared__ uint32_t s_cnt[];
+  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
+  __syncthreads();
+  const uint64_t tile = uint64_t(blockDim.x) * U;
+  for (uint64_t t0 = blockIdx.x * tile; t0 < n; t0 += uint64_t(gridDim.x) * tile) {
+    uint64_t v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
+      v[u] = i < n ? ld_stream_u64(keys + i) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
+      if (i < n) atomicAdd(&s_cnt[hash_primary<G>(d, v[u]).i1 >> shift], 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x)
+    if (s_cnt[s]) atomicAdd(&hist[s * kCtrStride], s_cnt[s]);
+}
+
+// ---------------------------------------------------------------------------
+// scan: exclusive prefix of the S counts in place (one block of 1024), and
+// the rec2 fill counters zeroed.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(1024)
+k_slice_scan(uint32_t* __restrict__ cursor, uint32_t S, uint32_t* __restrict__ fill2) {
+  __shared__ uint32_t warp_sum[32];
+  __shared__ uint32_t carry;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < S; base += blockDim.x) {
+    const uint32_t s = base + threadIdx.x;
+    const uint32_t v = s < S ? cursor[s * kCtrStride] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= uint32_t(o)) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t t = warp_sum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+        if (lane >= uint32_t(o)) t += y;
+      }
+      warp_sum[lane] = t;
+    }
+    __syncthreads();
+    if (s < S) cursor[s * kCtrStride] = carry + (warp ? warp_sum[warp - 1] : 0u) + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[31];
+    __syncthreads();
+  }
+  for (uint32_t s = threadIdx.x; s <= S; s += blockDim.x) fill2[s * kCtrStride] = 0;
+}
+
+// Exclusive prefix of in[0..S) into out[0..S) by the whole block (each
+// thread sums a run of consecutive bins, one warp scans the run sums).
+// Ends with a barrier; tmp is 32 words of shared memory.
+__device__ __forceinline__ void block_scan_excl(const uint32_t* in, uint32_t* out,
+                                                uint32_t S, uint32_t* tmp) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t per = (S + blockDim.x - 1) / blockDim.x;
+  const uint32_t b0 = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (uint32_t i = 0; i < per; ++i)
+    if (b0 + i < S) sum += in[b0 + i];
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= uint32_t(o)) x += y;
+  }
+  if (lane == 31) tmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < (blockDim.x >> 5) ? tmp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      if (lane >= uint32_t(o)) t += y;
+    }
+    tmp[lane] = t;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? tmp[warp - 1] : 0u) + x - sum;
+  for (uint32_t i = 0; i < per; ++i)
+    if (b0 + i < S) {
+      const uint32_t v = in[b0 + i];
+      out[b0 + i] = run;
+      run += v;
+    }
+  __syncthreads();
+}
+
+template <class G>
+__device__ __forceinline__ uint32_t slice_of_h(const DevFilter& d, uint64_t h,
+                                               uint32_t shift) {
+  return hash_from_h<G>(d, h).i1 >> shift;
+}
+
+// ---------------------------------------------------------------------------
+// scatter (a multi-split): each block tile of kBlock*U keys is binned by
+// slice in shared memory (a rank per key), sorted by slice inside shared
+// memory, and written out as one contiguous run per occupied slice (one
+// global cursor bump per run), so consecutive threads store consecutive
+// records.  dst[] is written in key order.
+// Shared memory: 3*S counters + 8*kBlock*U bytes.
+// ---------------------------------------------------------------------------
+template <class G, int U>
+__global__ void __launch_bounds__(kBlock)
+k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
+                uint32_t shift, uint32_t S, uint32_t* __restrict__ cursor,
+                uint64_t* __restrict__ rec1, uint32_t* __restrict__ dst) {
+  extern __shared__ uint64_t sm64[];
+  constexpr uint32_t T = kBlock * U;
+  uint64_t* stash = sm64;                                   // [T]
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(sm64 + T);  // [S]
+  uint32_t* s_off = s_cnt + S;                              // [S]
+  uint32_t* s_base = s_off + S;                             // [S]
+  __shared__ uint32_t tmp[32];
+  for (uint64_t t0 = blockIdx.x * uint64_t(T); t0 < n; t0 += uint64_t(gridDim.x) * T) {
+    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
+    __syncthreads();
+    uint64_t h[U];
+    uint32_t slrk[U];  // slice << 16 | rank
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
+      h[u] = i < n ? ld_stream_u64(keys + i) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
+      slrk[u] = 0;
+      if (i < n) {
+        h[u] = xxh64_u64(h[u]);
+        const uint32_t sl = slice_of_h<G>(d, h[u], shift);
+        slrk[u] = (sl << 16) | atomicAdd(&s_cnt[sl], 1u);
+      }
+    }
+    __syncthreads();
+    block_scan_excl(s_cnt, s_off, S, tmp);
+    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x)
+      if (s_cnt[s]) s_base[s] = atomicAdd(&cursor[s * kCtrStride], s_cnt[s]);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
+      if (i < n) {
+        const uint32_t sl = slrk[u] >> 16, rk = slrk[u] & 0xFFFFu;
+        stash[s_off[sl] + rk] = h[u];
+        if (dst) st_cs_u32(dst + i, s_base[sl] + rk);
+      }
+    }
+    __syncthreads();
+    const uint32_t cnt = uint32_t(n - t0 < T ? n - t0 : T);
+    for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const uint64_t hv = stash[j];
+      const uint32_t sl = slice_of_h<G>(d, hv, shift);
+      rec1[s_base[sl] + (j - s_off[sl])] = hv;
+    }
+    __syncthreads();
+  }
+}
+
+// rec2 position of the rk-th pending record of slice s in a block tile,
+// from the tile's claim (base = fill2[s] before the claim, cnt records):
+// the first cap2 - base go to the slice, the rest to the spill region.
+__device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
+                                             uint32_t base, uint32_t cnt,
+                                             uint32_t spill, uint64_t cap2,
+                                             uint32_t S) {
+  const uint64_t room = base >= cap2 ? 0 : cap2 - base;
+  const uint32_t in = room < cnt ? uint32_t(room) : cnt;
+  return rk < in ? uint64_t(s) * cap2 + base + rk
+                 : uint64_t(S) * cap2 + spill + (rk - in);
+}
+
+// ---------------------------------------------------------------------------
+// probe1: the operation on bucket i1 for rec1 records in order.  A block
+// tile is R rounds of kBlock*K records; records left pending are stashed in
+// shared memory and, once per tile, sorted by the slice of i2 and written to
+// rec2 as one run per occupied slice (one claim on fill2 per run).
+// Shared memory: 5*S counters + 14*T bytes (T = kBlock*K*R <= 2048).
+// ---------------------------------------------------------------------------
+template <class G, int OP, int K, int R>
+__global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
+k_slice_probe1(DevFilter d, SliceBufs sb, uint64_t n, int want_flags) {
+  constexpr uint32_t T = kBlock * K * R;
+  static_assert(T <= 2048, "stash entries pack an 11-bit tile index");
+  extern __shared__ uint64_t sm64[];
+  const uint32_t S = sb.n_slices;
+  uint64_t* stash_h = sm64;                                       // [T]
+  uint32_t* stash_pk = reinterpret_cast<uint32_t*>(sm64 + T);     // [T]
+  uint32_t* s_cnt = stash_pk + T;                                 // [S]
+  uint32_t* s_off = s_cnt + S;                                    // [S]
+  uint32_t* s_base = s_off + S;                                   // [S]
+  uint32_t* s_spill = s_base + S;                                 // [S]
+  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_spill + S);   // [T]
+  __shared__ uint32_t tmp[32];
+  __shared__ uint32_t s_n;
+  const uint32_t lane = threadIdx.x & 31;
+  TileCounts c;
+  const uint64_t step = uint64_t(gridDim.x) * T;
+  // All R*K records of the block's next tile are loaded while this tile's
+  // buckets are probed.
+  uint64_t hn[R * K];
+#pragma unroll
+  for (int k = 0; k < R * K; ++k) {
+    const uint64_t p = blockIdx.x * uint64_t(T) + uint64_t(k) * blockDim.x + threadIdx.x;
+    hn[k] = p < n ? ld_stream_u64(sb.rec1 + p) : 0ull;
+  }
+  for (uint64_t t0 = blockIdx.x * uint64_t(T); t0 < n; t0 += step) {
+    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    uint64_t hr[R * K];
+#pragma unroll
+    for (int k = 0; k < R * K; ++k) {
+      hr[k] = hn[k];
+      const uint64_t pn = t0 + step + uint64_t(k) * blockDim.x + threadIdx.x;
+      hn[k] = pn < n ? ld_stream_u64(sb.rec1 + pn) : 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      bool valid[K];
+      uint32_t bkt[K], tag[K];
+      int res[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const uint32_t loc = uint32_t(r * K + k) * blockDim.x + threadIdx.x;
+        valid[k] = t0 + loc < n;
+        const KeyHash kh = hash_from_h<G>(d, hr[r * K + k]);
+        bkt[k] = kh.i1;
+        tag[k] = kh.fp;
+      }
+      if constexpr (OP == SOP_CONTAINS) {
+        Bucket<G> bk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
+      } else {
+        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const uint32_t loc = uint32_t(r * K + k) * blockDim.x + threadIdx.x;
+        const bool pend = valid[k] && res[k] == TI_FULL;
+        // Stash slot: one shared atomic per warp.
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, pend);
+        uint32_t e0 = 0;
+        if (bal && lane == uint32_t(__ffs(bal) - 1)) e0 = atomicAdd(&s_n, uint32_t(__popc(bal)));
+        e0 = __shfl_sync(0xFFFFFFFFu, e0, __ffs(bal ? bal : 1u) - 1);
+        uint8_t v = 0;
+        if (pend) {
+          const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
+          const uint32_t rk = atomicAdd(&s_cnt[sl], 1u);
+          const uint32_t e = e0 + __popc(bal & ((1u << lane) - 1u));
+          stash_h[e] = hr[r * K + k];
+          stash_pk[e] = (sl << 22) | (rk << 11) | loc;
+          v = kPending;
+        } else if (valid[k]) {
+          if (res[k] == TI_OK) {
+            v = 1;
+            c.ok++;
+          } else {
+            v = 2;
+            c.cont++;
+            if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
+          }
+        }
+        if (valid[k] && want_flags) {
+          st_flag(sb.f1 + t0 + loc, v);
+          if (!pend) sb.link[t0 + loc] = 0u;
+        }
+      }
+    }
+    __syncthreads();
+    block_scan_excl(s_cnt, s_off, S, tmp);
+    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+      const uint32_t cnt = s_cnt[s];
+      if (!cnt) continue;
+      const uint32_t base = atomicAdd(&sb.fill2[s * kCtrStride], cnt);
+      const uint64_t room = base >= sb.cap2 ? 0 : sb.cap2 - base;
+      s_base[s] = base;
+      s_spill[s] = room < cnt ? atomicAdd(&sb.fill2[S * kCtrStride], cnt - uint32_t(room))
+                              : 0u;
+    }
+    const uint32_t np = s_n;
+    for (uint32_t e = threadIdx.x; e < np; e += blockDim.x) {
+      const uint32_t pk = stash_pk[e];
+      s_order[s_off[pk >> 22] + ((pk >> 11) & 0x7FFu)] = uint16_t(e);
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < np; j += blockDim.x) {
+      const uint32_t e = s_order[j];
+      const uint32_t pk = stash_pk[e];
+      const uint32_t sl = pk >> 22;
+      const uint64_t q = rec2_pos(sl, j - s_off[sl], s_base[sl], s_cnt[sl], s_spill[sl],
+                                  sb.cap2, S);
+      sb.rec2[q] = stash_h[e];
+      if (want_flags) sb.link[t0 + (pk & 0x7FFu)] = uint32_t(q);
+    }
+    __syncthreads();
+  }
+  if constexpr (OP == SOP_INSERT) {
+    block_add(&d.ctrl->occupancy, c.ok);
+    block_add(&d.ctrl->insert_ok, c.ok);
+    block_add(&d.ctrl->insert_fail, c.cont);
+    block_add(&d.ctrl->contention, c.cont);
+  } else if constexpr (OP == SOP_REMOVE) {
+    block_add(&d.ctrl->occupancy, c.ok, /*negate=*/true);
+    block_add(&d.ctrl->remove_ok, c.ok);
+    block_add(&d.ctrl->remove_fail, c.cont);
+    block_add(&d.ctrl->contention, c.cont);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// probe2: the operation on bucket i2 for the rec2 records, slice regions in
+// order, then the spill region.  Warp tiles of 32*K positions; positions
+// past a region's fill are skipped.
+// ---------------------------------------------------------------------------
+template <class G, int OP, int K>
+__global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
+k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
+               uint32_t* __restrict__ queue) {
+  const uint32_t S = sb.n_slices;
+  const uint64_t sliced = uint64_t(S) * sb.cap2;
+  const uint64_t span = sliced + n;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const uint32_t spill_n = __ldg(sb.fill2 + S * kCtrStride);
+  TileCounts c;
+  const QueuePush push{&d.ctrl->queue_count, queue};
+  for (uint64_t base = gw * (32u * K); base < span; base += nw * (32u * K)) {
+    bool valid[K];
+    uint64_t q[K];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      q[k] = base + uint64_t(k) * 32 + lane;
+      if (q[k] < sliced) {
+        const uint32_t s = uint32_t(q[k] / sb.cap2);
+        const uint64_t fill = __ldg(sb.fill2 + s * kCtrStride);
+        valid[k] = q[k] - uint64_t(s) * sb.cap2 < (fill < sb.cap2 ? fill : sb.cap2);
+      } else {
+        valid[k] = q[k] < span && q[k] - sliced < spill_n;
+      }
+      any |= valid[k];
+    }
+    if (!__any_sync(0xFFFFFFFFu, any)) continue;
+    uint32_t bkt[K], tag[K];
+    int r[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const KeyHash kh =
+          hash_from_h<G>(d, valid[k] ? ld_stream_u64(sb.rec2 + q[k]) : 0ull);
+      bkt[k] = alt_index<G>(d, kh.i1, kh.fp);
+      tag[k] = kh.fp | G::kChoice;
+    }
+    if constexpr (OP == SOP_CONTAINS) {
+      Bucket<G> bk[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (valid[k] && want_flags)
+          st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
+    } else {
+      cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, r);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        bool to_queue = false;
+        if (valid[k]) {
+          uint8_t v;
+          if (r[k] == TI_OK) {
+            v = 1;
+            c.ok++;
+          } else if (r[k] == TI_CONTENTION) {
+            v = 2;
+            c.cont++;
+            if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
+          } else {
+            v = 0;
+            if (OP == SOP_INSERT) to_queue = true;
+            else c.fail++;
+          }
+          if (want_flags && !to_queue) st_flag(sb.f2 + q[k], v);
+        }
+        if constexpr (OP == SOP_INSERT) push(to_queue, uint32_t(q[k]), lane);
+      }
+    }
+  }
+  if constexpr (OP == SOP_INSERT) {
+    block_add(&d.ctrl->occupancy, c.ok);
+    block_add(&d.ctrl->insert_ok, c.ok);
+    block_add(&d.ctrl->insert_fail, c.cont);
+    block_add(&d.ctrl->contention, c.cont);
+  } else if constexpr (OP == SOP_REMOVE) {
+    block_add(&d.ctrl->occupancy, c.ok, /*negate=*/true);
+    block_add(&d.ctrl->remove_ok, c.ok);
+    block_add(&d.ctrl->remove_fail, c.fail + c.cont);
+    block_add(&d.ctrl->contention, c.cont);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// merge: f1[p] = f2[link[p]] for pending records, four records per thread.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(kBlock)
+k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
+              const uint8_t* __restrict__ f2, uint64_t n) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t n4 = n / 4;
+  for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < n4; v += stride) {
+    uint32_t w = ld_cs_u32(reinterpret_cast<const uint32_t*>(f1) + v);
+    uint32_t pend = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (((w >> (8 * j)) & 0xFFu) == kPending) pend |= 1u << j;
+    if (!pend) continue;
+    const uint4 l = reinterpret_cast<const uint4*>(link)[v];
+    const uint32_t ls[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (pend & (1u << j))
+        w = (w & ~(0xFFu << (8 * j))) | (uint32_t(f2[ls[j]]) << (8 * j));
+    reinterpret_cast<uint32_t*>(f1)[v] = w;
+  }
+  for (uint64_t p = n4 * 4 + blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < n;
+       p += stride)
+    if (f1[p] == kPending) f1[p] = f2[link[p]];
+}
+
+// ---------------------------------------------------------------------------
+// out: flags[j] = f1[dst[j]], four keys per thread (byte stores when the
+// caller's flags are not 4-byte aligned).
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(kBlock)
+k_slice_out(const uint32_t* __restrict__ dst, const uint8_t* __restrict__ f1,
+            uint8_t* __restrict__ out, uint64_t n) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t n4 = n / 4;
+  const bool aligned = (reinterpret_cast<uintptr_t>(out) & 3u) == 0;
+  for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < n4; v += stride) {
+    const uint4 p = reinterpret_cast<const uint4*>(dst)[v];
+    const uint32_t b0 = f1[p.x], b1 = f1[p.y], b2 = f1[p.z], b3 = f1[p.w];
+    if (aligned) {
+      reinterpret_cast<uint32_t*>(out)[v] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+    } else {
+      out[4 * v] = uint8_t(b0);
+      out[4 * v + 1] = uint8_t(b1);
+      out[4 * v + 2] = uint8_t(b2);
+      out[4 * v + 3] = uint8_t(b3);
+    }
+  }
+  for (uint64_t j = n4 * 4 + blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; j < n;
+       j += stride)
+    out[j] = f1[dst[j]];
+}
+
+// ---------------------------------------------------------------------------
+// Launch sequence of one chunk.
+// ---------------------------------------------------------------------------
+template <class G>
+struct SliceLaunch {
+  static constexpr int KQ = Tiles<G, false>::K;
+  static constexpr int KM = Tiles<G, true>::K;
+  static constexpr int U = 16;  // keys per thread of a scatter tile
+
+  template <int OP, int K>
+  static cudaError_t probes(const DevFilter& d, const SliceBufs& sb, uint64_t n,
+                            int want, uint32_t* queue, cudaStream_t s,
+                            KernelTimer* t) {
+    constexpr int R = 8 / K;  // tiles of kBlock * 8 records
+    constexpr uint32_t T = kBlock * K * R;
+    const size_t smem = size_t(14) * T + size_t(16) * sb.n_slices;
+    auto p1 = k_slice_probe1<G, OP, K, R>;
+    if (t) t->begin(KK_SLICE_PROBE1, s);
+    p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, n, want);
+    if (t) t->end(KK_SLICE_PROBE1, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto p2 = k_slice_probe2<G, OP, K>;
+    const uint64_t span = uint64_t(sb.n_slices) * sb.cap2 + n;
+    if (t) t->begin(KK_SLICE_PROBE2, s);
+    p2<<<persistent_grid(p2, span, kBlock * K), kBlock, 0, s>>>(d, sb, n, want, queue);
+    if (t) t->end(KK_SLICE_PROBE2, s);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t run(const DevFilter& d, int op, const uint64_t* keys,
+                         uint64_t n, uint8_t* flags, const SliceBufs& sb,
+                         uint32_t* queue, cudaStream_t s, KernelTimer* t) {
+    const int want = flags != nullptr;
+    const uint32_t S = sb.n_slices;
+    if (t) t->begin(KK_SLICE_SPLIT, s);
+    cudaError_t e =
+        cudaMemsetAsync(sb.cursor, 0, size_t(S) * kCtrStride * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    auto fh = k_slice_hist<G, U>;
+    fh<<<persistent_grid(fh, n, kBlock * U), kBlock, S * sizeof(uint32_t), s>>>(
+        d, keys, n, sb.shift, S, sb.cursor);
+    k_slice_scan<<<1, 1024, 0, s>>>(sb.cursor, S, sb.fill2);
+    auto fs = k_slice_scatter<G, U>;
+    const size_t smem = size_t(8) * kBlock * U + size_t(12) * S;
+    fs<<<persistent_grid(fs, n, kBlock * U), kBlock, smem, s>>>(
+        d, keys, n, sb.shift, S, sb.cursor, sb.rec1, want ? sb.dst : nullptr);
+    if (t) t->end(KK_SLICE_SPLIT, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (op == SOP_CONTAINS)
+      e = probes<SOP_CONTAINS, KQ>(d, sb, n, want, queue, s, t);
+    else if (op == SOP_REMOVE)
+      e = probes<SOP_REMOVE, KM>(d, sb, n, want, queue, s, t);
+    else
+      e = probes<SOP_INSERT, KM>(d, sb, n, want, queue, s, t);
+    if (e != cudaSuccess) return e;
+    if (op == SOP_INSERT) {
+      auto fe = k_insert_evict<G, true>;
+      const int occ = cached_occupancy(reinterpret_cast<const void*>(fe), kBlock);
+      if (t) t->begin(KK_INSERT_EVICT, s);
+      fe<<<unsigned(device_sm_count() * (occ > 0 ? occ : 1)), kBlock, 0, s>>>(
+          d, sb.rec2, want ? sb.f2 : nullptr, nullptr, queue);
+      if (t) t->end(KK_INSERT_EVICT, s);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    if (!want) return cudaSuccess;
+    if (t) t->begin(KK_SLICE_MERGE, s);
+    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 4), kBlock, 0, s>>>(
+        sb.f1, sb.link, sb.f2, n);
+    k_slice_out<<<persistent_grid(k_slice_out, n, kBlock * 4), kBlock, 0, s>>>(
+        sb.dst, sb.f1, flags, n);
+    if (t) t->end(KK_SLICE_MERGE, s);
+    return cudaGetLastError();
+  }
+};
+
+template <class G>
+const Ops* ops_for() {
+  static const Ops o = {&Launch<G>::contains, &Launch<G>::remove,
+                        &Launch<G>::insert_chunk, &Launch<G>::insert_serial,
+                        &Launch<G>::hash, &Launch<G>::count, &SliceLaunch<G>::run};
+  return &o;
+}
+
+}  // namespace cfk

@@ -48,4 +48,22 @@ struct DevFilter {
   uint32_t pad;
 };
 
+constexpr uint32_t kSliceMax = 1024;  // slices per table (shared-memory bins)
+
+// Device scratch of the slice-partitioned path for chunks of up to n keys
+// (see cf_slice.cuh).
+struct SliceBufs {
+  uint32_t n_slices;  // S
+  uint32_t shift;     // slice of bucket j = j >> shift
+  uint64_t cap2;      // rec2 records per slice (the spill region follows)
+  uint32_t* cursor;   // [S * 32] histogram, then scatter cursors (one per line)
+  uint32_t* fill2;    // [(S + 1) * 32] rec2 records claimed per slice; slice S = spill
+  uint32_t* dst;      // [n]     rec1 position of key j
+  uint64_t* rec1;     // [n]     key hashes grouped by the slice of i1
+  uint8_t* f1;        // [n]     result of probe1 (kPending: see link / f2)
+  uint32_t* link;     // [n]     rec2 position of a pending rec1 record
+  uint64_t* rec2;     // [S * cap2 + n] pending records grouped by i2's slice
+  uint8_t* f2;        // [S * cap2 + n] result of probe2 / the eviction loop
+};
+
 }  // namespace cfk

@@ -188,6 +188,13 @@ class CuckooFilter:
     def set_staging_chunk(self, keys_per_chunk: int):
         check(self._L.cf_set_staging_chunk(self._h, int(keys_per_chunk)), "cf_set_staging_chunk")
 
+    def set_slicing(self, mode: str = "auto", slice_bytes: int = 0, max_chunk: int = 0):
+        """Slice-partitioned execution (cf_set_slicing): mode "off", "auto"
+        or "always"; slice_bytes / max_chunk 0 take the library defaults."""
+        code = {"off": 0, "auto": 1, "always": 2}[mode]
+        check(self._L.cf_set_slicing(self._h, code, int(slice_bytes), int(max_chunk)),
+              "cf_set_slicing")
+
     # ---- state -----------------------------------------------------------------
     def clear(self, stream=None):
         check(self._L.cf_clear(self._h, _stream_handle(stream)), "cf_clear")

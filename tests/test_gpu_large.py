@@ -1,8 +1,9 @@
 """The large-filter workload at full size (2^28 buckets x 4, f16, fill to
 LF 0.95 in three calls, 2^30 queries at a 50% positive mix, 2^28 deletes),
-in the launch configuration bench.py times.  The oracle cannot replay a
-billion inserts, so outputs are checked on samples it can compute one by
-one, and by properties that hold at any size:
+in the launch configuration bench.py times (the slice-partitioned path,
+which the library picks for a table of this size).  The oracle cannot
+replay a billion inserts, so outputs are checked on samples it can compute
+one by one, and by properties that hold at any size:
 
   * hash: (fp, i1, i2) of 2^20 sampled keys bit-exact with the oracle;
   * query: for sampled queries, the flag equals the definition of Alg. 2
@@ -73,9 +74,17 @@ def test_large_workload_full_size():
     assert np.array_equal(gi1.cpu().numpy().view(np.uint64), oi1)
     assert np.array_equal(gi2.cpu().numpy().view(np.uint64), oi2)
 
-    # Queries (bench launch: one cf_contains over 2^30 keys).
+    # Queries (bench launch: one cf_contains over 2^30 keys; the 2 GiB table
+    # takes the slice-partitioned path by default).
     qf = g.contains(queries, stream=stream)
     stream.synchronize()
+    # The plain kernels give the same 2^30 flags.
+    g.set_slicing("off")
+    qf_plain = g.contains(queries, stream=stream)
+    stream.synchronize()
+    assert torch.equal(qf, qf_plain)
+    del qf_plain
+    g.set_slicing("auto")
     slots = _table_slots(g)
     qpick = np.sort(rng.choice(W.n_queries, size=1 << 20, replace=False))
     qk = queries[torch.from_numpy(qpick).cuda()].cpu().numpy().view(np.uint64)
