@@ -40,20 +40,33 @@ struct BatchCtl {
 };
 static_assert(sizeof(BatchCtl) == 64, "batch header is 64 bytes");
 
-// Appends (item, key index) to the combined eviction queue.
+// Appends (item, key index) to the combined eviction queue: one atomic per
+// warp tile.
 struct BatchPush {
   unsigned int* count;
   uint2* queue;
   uint32_t item;
-  __device__ __forceinline__ void operator()(bool need, uint32_t idx,
-                                             uint32_t lane) const {
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
-    if (!bal) return;
-    const int leader = __ffs(bal) - 1;
+  template <int K>
+  __device__ __forceinline__ void push_all(const bool (&need)[K],
+                                           const uint32_t (&idx)[K],
+                                           uint32_t lane) const {
+    unsigned bal[K];
+    uint32_t total = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      bal[k] = __ballot_sync(0xFFFFFFFFu, need[k]);
+      total += __popc(bal[k]);
+    }
+    if (!total) return;
     uint32_t pos = 0;
-    if (int(lane) == leader) pos = atomicAdd(count, __popc(bal));
-    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-    if (need) queue[pos + __popc(bal & ((1u << lane) - 1u))] = make_uint2(item, idx);
+    if (lane == 0) pos = atomicAdd(count, total);
+    pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (need[k]) queue[pos + __popc(bal[k] & lt)] = make_uint2(item, idx[k]);
+      pos += __popc(bal[k]);
+    }
   }
 };
 

@@ -31,6 +31,21 @@ constexpr int kBlock = 256;
 #ifndef CF_MINB_MUT
 #define CF_MINB_MUT 2
 #endif
+// BFS frontier width of the single-filter eviction kernel: the number of
+// candidates whose alternate buckets are loaded together (CF_EVICT_FW; 0 or
+// an invalid value means b/2, all at once).
+#ifndef CF_EVICT_FW
+#define CF_EVICT_FW 0
+#endif
+template <class G>
+struct EvictFW {
+  static constexpr int H = G::B / 2;
+  static constexpr int value =
+      (CF_EVICT_FW > 0 && CF_EVICT_FW <= H && H % (CF_EVICT_FW > 0 ? CF_EVICT_FW : 1) == 0)
+          ? CF_EVICT_FW
+          : H;
+};
+
 template <class G, bool MUT>
 struct Tiles {
   static constexpr int K = G::kBucketBytes <= 8 ? (MUT ? CF_K_MUT : CF_K_QUERY)
@@ -212,19 +227,33 @@ struct TileCounts {
   uint32_t ok = 0, fail = 0, cont = 0;
 };
 
-// Appends key indices to a filter's eviction queue: one atomic per warp.
+// Appends key indices to a filter's eviction queue: the K keys of every
+// lane of a warp tile with one atomic on the queue counter (a single
+// counter that all warps share).
 struct QueuePush {
   unsigned int* count;
   uint32_t* queue;
-  __device__ __forceinline__ void operator()(bool need, uint32_t idx,
-                                             uint32_t lane) const {
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
-    if (!bal) return;
-    const int leader = __ffs(bal) - 1;
+  template <int K>
+  __device__ __forceinline__ void push_all(const bool (&need)[K],
+                                           const uint32_t (&idx)[K],
+                                           uint32_t lane) const {
+    unsigned bal[K];
+    uint32_t total = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      bal[k] = __ballot_sync(0xFFFFFFFFu, need[k]);
+      total += __popc(bal[k]);
+    }
+    if (!total) return;
     uint32_t pos = 0;
-    if (int(lane) == leader) pos = atomicAdd(count, __popc(bal));
-    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-    if (need) queue[pos + __popc(bal & ((1u << lane) - 1u))] = idx;
+    if (lane == 0) pos = atomicAdd(count, total);
+    pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (need[k]) queue[pos + __popc(bal[k] & lt)] = idx[k];
+      pos += __popc(bal[k]);
+    }
   }
 };
 
@@ -263,9 +292,13 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
     }
   }
   cas_many<G, K, true>(d, bkt, tag, act, r2);
+  bool need[K];
+  uint32_t qidx[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint32_t idx = uint32_t(base + uint64_t(k) * 32 + lane);
+    need[k] = act[k] && r2[k] == TI_FULL;
+    qidx[k] = idx;
     const bool ok = valid[k] && (r1[k] == TI_OK || (act[k] && r2[k] == TI_OK));
     const bool cont = valid[k] && (r1[k] == TI_CONTENTION ||
                                    (act[k] && r2[k] == TI_CONTENTION));
@@ -280,8 +313,8 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
       if (flags) st_flag(flags + idx, 2);
       if (evout) evout[idx] = 0;
     }
-    push(act[k] && r2[k] == TI_FULL, idx, lane);
   }
+  push.push_all(need, qidx, lane);
 }
 
 // Query (Alg. 2): Find(i1) or Find(i2).  All K first-bucket loads of a
@@ -468,7 +501,7 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
     if (active) {
       uint32_t vt = 0;
       uint64_t vb = 0;
-      const int r = evict_round<G>(d, c, vt, vb, ec);
+      const int r = evict_round<G, EvictFW<G>::value>(d, c, vt, vb, ec);
       if (r != ROUND_CONTINUE) {
         if (r != EV_OK) log_victim(d, vt, vb);
         if (flags) st_flag(flags + idx, uint8_t(r));

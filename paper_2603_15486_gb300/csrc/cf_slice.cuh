@@ -406,32 +406,44 @@ template <class G, int OP, int K>
 __global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
 k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
                uint32_t* __restrict__ queue) {
+  // The filled part of each region (S slices, then the spill region) and
+  // its start in the compacted order, so that warps walk only records.
+  extern __shared__ uint32_t s_reg[];
+  __shared__ uint32_t tmp[32];
   const uint32_t S = sb.n_slices;
-  const uint64_t sliced = uint64_t(S) * sb.cap2;
-  const uint64_t span = sliced + n;
+  const uint32_t NR = S + 1;
+  uint32_t* s_len = s_reg;
+  uint32_t* s_start = s_reg + NR;
+  for (uint32_t r = threadIdx.x; r < NR; r += blockDim.x) {
+    const uint32_t fill = __ldg(sb.fill2 + r * kCtrStride);
+    s_len[r] = r < S ? (fill < sb.cap2 ? fill : uint32_t(sb.cap2)) : fill;
+  }
+  __syncthreads();
+  block_scan_excl(s_len, s_start, NR, tmp);
+  const uint64_t total = uint64_t(s_start[NR - 1]) + s_len[NR - 1];
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  const uint32_t spill_n = __ldg(sb.fill2 + S * kCtrStride);
   TileCounts c;
   const QueuePush push{&d.ctrl->queue_count, queue};
-  for (uint64_t base = gw * (32u * K); base < span; base += nw * (32u * K)) {
+  for (uint64_t base = gw * (32u * K); base < total; base += nw * (32u * K)) {
     bool valid[K];
     uint64_t q[K];
-    bool any = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      q[k] = base + uint64_t(k) * 32 + lane;
-      if (q[k] < sliced) {
-        const uint32_t s = uint32_t(q[k] / sb.cap2);
-        const uint64_t fill = __ldg(sb.fill2 + s * kCtrStride);
-        valid[k] = q[k] - uint64_t(s) * sb.cap2 < (fill < sb.cap2 ? fill : sb.cap2);
-      } else {
-        valid[k] = q[k] < span && q[k] - sliced < spill_n;
+      const uint64_t x = base + uint64_t(k) * 32 + lane;
+      valid[k] = x < total;
+      q[k] = 0;
+      if (valid[k]) {
+        // The last region starting at or before x holds it.
+        uint32_t lo = 0, hi = NR;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (s_start[mid] <= x) lo = mid; else hi = mid;
+        }
+        q[k] = uint64_t(lo) * sb.cap2 + (x - s_start[lo]);
       }
-      any |= valid[k];
     }
-    if (!__any_sync(0xFFFFFFFFu, any)) continue;
     uint32_t bkt[K], tag[K];
     int r[K];
 #pragma unroll
@@ -452,9 +464,12 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
           st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
     } else {
       cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, r);
+      bool to_queue[K];
+      uint32_t qidx[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        bool to_queue = false;
+        to_queue[k] = false;
+        qidx[k] = uint32_t(q[k]);
         if (valid[k]) {
           uint8_t v;
           if (r[k] == TI_OK) {
@@ -466,13 +481,13 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
             if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
           } else {
             v = 0;
-            if (OP == SOP_INSERT) to_queue = true;
+            if (OP == SOP_INSERT) to_queue[k] = true;
             else c.fail++;
           }
-          if (want_flags && !to_queue) st_flag(sb.f2 + q[k], v);
+          if (want_flags && !to_queue[k]) st_flag(sb.f2 + q[k], v);
         }
-        if constexpr (OP == SOP_INSERT) push(to_queue, uint32_t(q[k]), lane);
       }
+      if constexpr (OP == SOP_INSERT) push.push_all(to_queue, qidx, lane);
     }
   }
   if constexpr (OP == SOP_INSERT) {
@@ -489,27 +504,49 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
 }
 
 // ---------------------------------------------------------------------------
-// merge: f1[p] = f2[link[p]] for pending records, four records per thread.
+// merge: f1[p] = f2[link[p]] for pending records.  A thread takes V groups of
+// four records per iteration (V grid strides apart), so that up to 4*V of
+// its gathers are in flight together.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pending_mask(uint32_t w) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (((w >> (8 * j)) & 0xFFu) == kPending) m |= 1u << j;
+  return m;
+}
+
 static __global__ void __launch_bounds__(kBlock)
 k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
               const uint8_t* __restrict__ f2, uint64_t n) {
+  constexpr int V = 4;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t n4 = n / 4;
-  for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < n4; v += stride) {
-    uint32_t w = ld_cs_u32(reinterpret_cast<const uint32_t*>(f1) + v);
-    uint32_t pend = 0;
+  uint32_t* f1w = reinterpret_cast<uint32_t*>(f1);
+  const uint4* link4 = reinterpret_cast<const uint4*>(link);
+  for (uint64_t v0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v0 < n4;
+       v0 += stride * V) {
+    uint32_t w[V], pend[V];
+    uint4 l[V];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (((w >> (8 * j)) & 0xFFu) == kPending) pend |= 1u << j;
-    if (!pend) continue;
-    const uint4 l = reinterpret_cast<const uint4*>(link)[v];
-    const uint32_t ls[4] = {l.x, l.y, l.z, l.w};
+    for (int u = 0; u < V; ++u) {
+      const uint64_t v = v0 + u * stride;
+      w[u] = v < n4 ? ld_cs_u32(f1w + v) : 0u;
+      pend[u] = v < n4 ? pending_mask(w[u]) : 0u;
+    }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (pend & (1u << j))
-        w = (w & ~(0xFFu << (8 * j))) | (uint32_t(f2[ls[j]]) << (8 * j));
-    reinterpret_cast<uint32_t*>(f1)[v] = w;
+    for (int u = 0; u < V; ++u)
+      if (pend[u]) l[u] = link4[v0 + u * stride];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      if (!pend[u]) continue;
+      const uint32_t ls[4] = {l[u].x, l[u].y, l[u].z, l[u].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (pend[u] & (1u << j))
+          w[u] = (w[u] & ~(0xFFu << (8 * j))) | (uint32_t(f2[ls[j]]) << (8 * j));
+      f1w[v0 + u * stride] = w[u];
+    }
   }
   for (uint64_t p = n4 * 4 + blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < n;
        p += stride)
@@ -517,25 +554,36 @@ k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
 }
 
 // ---------------------------------------------------------------------------
-// out: flags[j] = f1[dst[j]], four keys per thread (byte stores when the
-// caller's flags are not 4-byte aligned).
+// out: flags[j] = f1[dst[j]], V groups of four keys per thread and iteration
+// (byte stores when the caller's flags are not 4-byte aligned).
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(kBlock)
 k_slice_out(const uint32_t* __restrict__ dst, const uint8_t* __restrict__ f1,
             uint8_t* __restrict__ out, uint64_t n) {
+  constexpr int V = 4;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t n4 = n / 4;
   const bool aligned = (reinterpret_cast<uintptr_t>(out) & 3u) == 0;
-  for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < n4; v += stride) {
-    const uint4 p = reinterpret_cast<const uint4*>(dst)[v];
-    const uint32_t b0 = f1[p.x], b1 = f1[p.y], b2 = f1[p.z], b3 = f1[p.w];
-    if (aligned) {
-      reinterpret_cast<uint32_t*>(out)[v] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-    } else {
-      out[4 * v] = uint8_t(b0);
-      out[4 * v + 1] = uint8_t(b1);
-      out[4 * v + 2] = uint8_t(b2);
-      out[4 * v + 3] = uint8_t(b3);
+  const uint4* dst4 = reinterpret_cast<const uint4*>(dst);
+  for (uint64_t v0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v0 < n4;
+       v0 += stride * V) {
+    uint4 p[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+      if (v0 + u * stride < n4) p[u] = dst4[v0 + u * stride];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      const uint64_t v = v0 + u * stride;
+      if (v >= n4) continue;
+      const uint32_t b0 = f1[p[u].x], b1 = f1[p[u].y], b2 = f1[p[u].z], b3 = f1[p[u].w];
+      if (aligned) {
+        reinterpret_cast<uint32_t*>(out)[v] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+      } else {
+        out[4 * v] = uint8_t(b0);
+        out[4 * v + 1] = uint8_t(b1);
+        out[4 * v + 2] = uint8_t(b2);
+        out[4 * v + 3] = uint8_t(b3);
+      }
     }
   }
   for (uint64_t j = n4 * 4 + blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; j < n;
@@ -549,7 +597,6 @@ k_slice_out(const uint32_t* __restrict__ dst, const uint8_t* __restrict__ f1,
 template <class G>
 struct SliceLaunch {
   static constexpr int KQ = Tiles<G, false>::K;
-  static constexpr int KM = Tiles<G, true>::K;
   static constexpr int U = 16;  // keys per thread of a scatter tile
 
   template <int OP, int K>
@@ -566,9 +613,9 @@ struct SliceLaunch {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto p2 = k_slice_probe2<G, OP, K>;
-    const uint64_t span = uint64_t(sb.n_slices) * sb.cap2 + n;
+    const size_t smem2 = size_t(2) * (sb.n_slices + 1) * sizeof(uint32_t);
     if (t) t->begin(KK_SLICE_PROBE2, s);
-    p2<<<persistent_grid(p2, span, kBlock * K), kBlock, 0, s>>>(d, sb, n, want, queue);
+    p2<<<persistent_grid(p2, n, kBlock * K), kBlock, smem2, s>>>(d, sb, n, want, queue);
     if (t) t->end(KK_SLICE_PROBE2, s);
     return cudaGetLastError();
   }
@@ -593,12 +640,15 @@ struct SliceLaunch {
     if (t) t->end(KK_SLICE_SPLIT, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // All three operations take the query's K (8 for 8-byte buckets): the
+    // bucket accesses hit L2 here, so the mutating passes are latency-bound
+    // and want every key's load and CAS of a tile in flight together.
     if (op == SOP_CONTAINS)
       e = probes<SOP_CONTAINS, KQ>(d, sb, n, want, queue, s, t);
     else if (op == SOP_REMOVE)
-      e = probes<SOP_REMOVE, KM>(d, sb, n, want, queue, s, t);
+      e = probes<SOP_REMOVE, KQ>(d, sb, n, want, queue, s, t);
     else
-      e = probes<SOP_INSERT, KM>(d, sb, n, want, queue, s, t);
+      e = probes<SOP_INSERT, KQ>(d, sb, n, want, queue, s, t);
     if (e != cudaSuccess) return e;
     if (op == SOP_INSERT) {
       auto fe = k_insert_evict<G, true>;
@@ -612,9 +662,9 @@ struct SliceLaunch {
     }
     if (!want) return cudaSuccess;
     if (t) t->begin(KK_SLICE_MERGE, s);
-    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 4), kBlock, 0, s>>>(
+    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 16), kBlock, 0, s>>>(
         sb.f1, sb.link, sb.f2, n);
-    k_slice_out<<<persistent_grid(k_slice_out, n, kBlock * 4), kBlock, 0, s>>>(
+    k_slice_out<<<persistent_grid(k_slice_out, n, kBlock * 16), kBlock, 0, s>>>(
         sb.dst, sb.f1, flags, n);
     if (t) t->end(KK_SLICE_MERGE, s);
     return cudaGetLastError();
