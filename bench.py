@@ -268,7 +268,7 @@ def gpu_arm(args):
     q_flags = torch.empty(W.n_queries, dtype=torch.uint8, device=dev)
     d_flags = torch.empty(W.n_deletes, dtype=torch.uint8, device=dev)
     filt = CuckooFilter(W.m, W.f, W.b, W.max_evictions)
-    filt.set_slicing(args.slicing, 0, args.slice_chunk)
+    filt.set_slicing(args.slicing, args.slice_bytes, args.slice_chunk)
     stream.synchronize()
 
     segs = W.insert_segments()
@@ -359,6 +359,7 @@ def gpu_arm(args):
                    "keys": "splitmix64 seed 2, uniform uint64",
                    "parallelism": f"replicas x{ws}",
                    "slicing": args.slicing, "slice_chunk": args.slice_chunk or (1 << 28),
+                   "slice_bytes": args.slice_bytes or (32 << 20),
                    "l2": "no flush: 2 GiB table and 8 GB key arrays exceed the 129 MB L2"},
         "phases": {k: {"ms": round(v * 1e3, 3),
                        "mops": round(n / v / 1e6, 1)}
@@ -476,7 +477,7 @@ def e2e_run(filt, keys, queries, W, args, stream):
     hk.copy_(keys)
     hq.copy_(queries)
     segs = W.insert_segments()
-    filt.set_staging_chunk(1 << 24)
+    filt.set_staging_chunk(args.e2e_chunk)
 
     def step():
         filt.clear(stream=stream)
@@ -501,6 +502,7 @@ def e2e_run(filt, keys, queries, W, args, stream):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "steps": args.e2e_steps, "pinned": pinned,
             "ms_per_step": round(el / args.e2e_steps * 1e3, 3),
+            "staging_chunk": args.e2e_chunk,
             "api": "cf_insert_host / cf_contains_host / cf_remove_host"}
 
 
@@ -899,11 +901,15 @@ def probe_arm(args):
                 buf.data_ptr(), buf.numel(), n, ab, lp, seed, sink.data_ptr(), sh))
     l2 = timed(lambda seed: L.cf_probe_gather(buf.data_ptr(), 1 << 26, n, 8, 8, seed,
                                               sink.data_ptr(), sh))
+    # The same load forms and the atomic over a 16 MiB region (L2-resident:
+    # the rate a slice-grouped pass can reach).
+    l2_forms = {FLAVOURS[fl]: timed(lambda seed, fl=fl: L.cf_probe_gather_flavour(
+        buf.data_ptr(), 16 << 20, n, fl, seed, sink.data_ptr(), sh)) for fl in (0, 1, 9)}
     return {"metric": "random load rate (G loads/s) over a 2 GiB buffer", "mode": "probe",
             "unit": "G loads/s", "value": by_flavour[FLAVOURS[0]], "n_gpus": 1,
             "higher_is_better": True, "config": {"loads": n, "buffer_bytes": 1 << 31},
             "by_load_form": by_flavour, "by_size_and_loads_in_flight": by_shape,
-            "l2_resident_64MiB_8B_x8": l2}
+            "l2_resident_64MiB_8B_x8": l2, "l2_resident_16MiB_by_form": l2_forms}
 
 
 def main(argv=None):
@@ -925,8 +931,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-warmup", type=int, default=1)
+    ap.add_argument("--e2e-chunk", type=int, default=1 << 26,
+                    help="keys per staging chunk of the host-buffer calls")
     ap.add_argument("--slicing", choices=["off", "auto", "always"], default="auto",
                     help="slice-partitioned execution of the filter calls (cf_set_slicing)")
+    ap.add_argument("--slice-bytes", type=int, default=0,
+                    help="table bytes per slice (0: the library default, 32 MiB)")
     ap.add_argument("--slice-chunk", type=int, default=0,
                     help="keys per sliced pass (0: the library default, 2^28)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -184,7 +184,7 @@ cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk);
  *  - mode: 0 never, 1 automatic (the default: tables of at least 512 MiB and
  *    batches of at least num_buckets / 8 keys), 2 always.
  *  - slice_bytes: table bytes per slice, rounded down to a power-of-two
- *    number of buckets (0: 16 MiB).  At most 1024 slices: larger tables get
+ *    number of buckets (0: 32 MiB).  At most 1024 slices: larger tables get
  *    larger slices.  CF_EINVAL if smaller than one bucket.
  *  - max_chunk: keys per sliced pass (0: 2^28, at most 2^30, CF_EINVAL
  *    above).  Larger batches run as consecutive passes.

@@ -136,6 +136,31 @@ __device__ __forceinline__ Bucket<G> load_bucket(const typename G::Word* p) {
   return b;
 }
 
+// Bucket loads of the eviction chains: random, one use each, so with
+// CF_EVICT_L2_64B the L2 fetch of a miss is limited to 64 bytes (two
+// sectors) instead of the default 128 (one-word buckets only).
+#ifndef CF_EVICT_L2_64B
+#define CF_EVICT_L2_64B 0
+#endif
+template <class G>
+__device__ __forceinline__ Bucket<G> load_bucket_ev(const typename G::Word* p) {
+  if constexpr (CF_EVICT_L2_64B && G::kWpb == 1) {
+    Bucket<G> b;
+    if constexpr (G::kW32) {
+      unsigned int v;
+      asm volatile("ld.global.cg.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+      b.w[0] = v;
+    } else {
+      unsigned long long v;
+      asm volatile("ld.global.cg.L2::64B.u64 %0, [%1];" : "=l"(v) : "l"(p));
+      b.w[0] = v;
+    }
+    return b;
+  } else {
+    return load_bucket<G, false>(p);
+  }
+}
+
 template <class G>
 __device__ __forceinline__ typename G::Word select_word(const Bucket<G>& b,
                                                         int wi) {
@@ -494,7 +519,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
     Bucket<G> ab[FW];
 #pragma unroll
     for (int q = 0; q < FW; ++q)
-      if (cand[g + q]) ab[q] = load_bucket<G, false>(bucket_ptr<G>(d, a[g + q]));
+      if (cand[g + q]) ab[q] = load_bucket_ev<G>(bucket_ptr<G>(d, a[g + q]));
 #pragma unroll
     for (int q = 0; q < FW; ++q) {
       if (!open && cand[g + q] && has_empty<G>(ab[q])) {
@@ -534,7 +559,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   if (open && evicted == t[chosen])
     c.bk = tb;  // the probe's words of that very bucket
   else
-    c.bk = load_bucket<G, false>(bucket_ptr<G>(d, c.cur));
+    c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
   const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk);
   if (r == TI_OK) return EV_OK;
   if (r == TI_CONTENTION) {
@@ -580,7 +605,7 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   uint32_t moved;
   c.cur = alt_of<G>(d, c.cur, evicted, moved);
   c.tag = moved;
-  c.bk = load_bucket<G, false>(bucket_ptr<G>(d, c.cur));
+  c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
   const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk);
   if (r == TI_OK) return EV_OK;
   if (r == TI_CONTENTION) {
@@ -603,7 +628,7 @@ __device__ __forceinline__ Chain<G> chain_start(const DevFilter& d,
   c.cur = first ? kh.i1 : kh.i2;
   c.tag = first ? kh.fp : (kh.fp | G::kChoice);
   c.ev = 0;
-  c.bk = load_bucket<G, false>(bucket_ptr<G>(d, c.cur));
+  c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
   return c;
 }
 

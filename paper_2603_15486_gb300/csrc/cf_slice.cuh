@@ -49,6 +49,8 @@ constexpr uint8_t kPending = 0xFF;
 // apart): every block tile bumps one counter per slice, and counters packed
 // into a few lines would serialise those atomics on a few L2 slices.
 constexpr uint32_t kCtrStride = 32;
+// fill2 holds S per-slice counters, then the spill count (index S) and the
+// dynamic tile counters of probe2 (S + 1) and probe1 (S + 2): kFill2Extra.
 
 enum : int { SOP_INSERT = 0, SOP_CONTAINS = 1, SOP_REMOVE = 2 };
 
@@ -93,7 +95,7 @@ k_slice_hist(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
 
 // ---------------------------------------------------------------------------
 // scan: exclusive prefix of the S counts in place (one block of 1024), and
-// the rec2 fill counters zeroed.
+// the rec2 fill counters and tile counters zeroed.
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(1024)
 k_slice_scan(uint32_t* __restrict__ cursor, uint32_t S, uint32_t* __restrict__ fill2) {
@@ -128,7 +130,7 @@ k_slice_scan(uint32_t* __restrict__ cursor, uint32_t S, uint32_t* __restrict__ f
     if (threadIdx.x == 0) carry += warp_sum[31];
     __syncthreads();
   }
-  for (uint32_t s = threadIdx.x; s <= S; s += blockDim.x) fill2[s * kCtrStride] = 0;
+  for (uint32_t s = threadIdx.x; s < S + kFill2Extra; s += blockDim.x) fill2[s * kCtrStride] = 0;
 }
 
 // Exclusive prefix of in[0..S) into out[0..S) by the whole block (each
@@ -256,104 +258,116 @@ __device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
 
 // ---------------------------------------------------------------------------
 // probe1: the operation on bucket i1 for rec1 records in order.  A block
-// tile is R rounds of kBlock*K records; records left pending are stashed in
-// shared memory and, once per tile, sorted by the slice of i2 and written to
+// tile is kBlock*K records, thread t owning the K consecutive records
+// t*K .. t*K+K-1 (vector loads of rec1, one 8-byte store of their flags, two
+// 16-byte stores of their links).  Records left pending are stashed in
+// shared memory, sorted by the slice of i2 once per tile, and written to
 // rec2 as one run per occupied slice (one claim on fill2 per run).
-// Shared memory: 5*S counters + 14*T bytes (T = kBlock*K*R <= 2048).
+// Shared memory: 12*T bytes + 4*S counters (T = kBlock*K <= 2048).
 // ---------------------------------------------------------------------------
-template <class G, int OP, int K, int R>
+__device__ __forceinline__ void ld_cs_v2_u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.global.cs.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+__device__ __forceinline__ void st_v4_u32(uint32_t* p, uint32_t a, uint32_t b, uint32_t c,
+                                          uint32_t e) {
+  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
+               "r"(e));
+}
+__device__ __forceinline__ void st_cs_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
+
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+template <class G, int OP, int K>
 __global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
-k_slice_probe1(DevFilter d, SliceBufs sb, uint64_t n, int want_flags) {
-  constexpr uint32_t T = kBlock * K * R;
-  static_assert(T <= 2048, "stash entries pack an 11-bit tile index");
+k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
+  constexpr uint32_t T = kBlock * K;
+  static_assert(K == 8 || K == 4 || K == 2 || K == 1, "records per thread");
+  static_assert(T <= 2048, "shared entries pack an 11-bit tile index");
   extern __shared__ uint64_t sm64[];
   const uint32_t S = sb.n_slices;
-  uint64_t* stash_h = sm64;                                       // [T]
-  uint32_t* stash_pk = reinterpret_cast<uint32_t*>(sm64 + T);     // [T]
-  uint32_t* s_cnt = stash_pk + T;                                 // [S]
-  uint32_t* s_off = s_cnt + S;                                    // [S]
-  uint32_t* s_base = s_off + S;                                   // [S]
-  uint32_t* s_spill = s_base + S;                                 // [S]
-  uint16_t* s_order = reinterpret_cast<uint16_t*>(s_spill + S);   // [T]
+  uint64_t* stash_h = sm64;                                     // [T] by tile index
+  uint32_t* s_order = reinterpret_cast<uint32_t*>(sm64 + T);   // [T] index | slice << 11
+  uint32_t* s_cnt = s_order + T;                                // [S]
+  uint32_t* s_off = s_cnt + S;                                  // [S]
+  uint32_t* s_base = s_off + S;                                 // [S]
+  uint32_t* s_spill = s_base + S;                               // [S]
   __shared__ uint32_t tmp[32];
-  __shared__ uint32_t s_n;
-  const uint32_t lane = threadIdx.x & 31;
+  __shared__ uint32_t s_tile;
   TileCounts c;
-  const uint64_t step = uint64_t(gridDim.x) * T;
-  // All R*K records of the block's next tile are loaded while this tile's
-  // buckets are probed.
-  uint64_t hn[R * K];
-#pragma unroll
-  for (int k = 0; k < R * K; ++k) {
-    const uint64_t p = blockIdx.x * uint64_t(T) + uint64_t(k) * blockDim.x + threadIdx.x;
-    hn[k] = p < n ? ld_stream_u64(sb.rec1 + p) : 0ull;
-  }
-  for (uint64_t t0 = blockIdx.x * uint64_t(T); t0 < n; t0 += step) {
+  const uint32_t me = threadIdx.x * K;  // first tile index of this thread
+  // Tiles are handed out in order by a counter, so the blocks at work stay
+  // within a window of consecutive tiles (one or two slices) instead of
+  // drifting apart as a static grid stride lets them.
+  uint32_t* tile_ctr = sb.fill2 + (S + 2) * kCtrStride;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
     for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
-    if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
-    uint64_t hr[R * K];
+    const uint32_t t0 = s_tile * T;
+    if (t0 >= n) break;
+    const uint32_t p0 = t0 + me;
+    const bool full = p0 + K <= n;
+    uint64_t h[K];
+    if (full && K % 2 == 0) {
 #pragma unroll
-    for (int k = 0; k < R * K; ++k) {
-      hr[k] = hn[k];
-      const uint64_t pn = t0 + step + uint64_t(k) * blockDim.x + threadIdx.x;
-      hn[k] = pn < n ? ld_stream_u64(sb.rec1 + pn) : 0ull;
+      for (int k = 0; k + 1 < K; k += 2) ld_cs_v2_u64(sb.rec1 + p0 + k, h[k], h[k + 1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) h[k] = p0 + k < n ? ld_stream_u64(sb.rec1 + p0 + k) : 0ull;
     }
+    bool valid[K];
+    uint32_t bkt[K], tag[K];
+    int res[K];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      bool valid[K];
-      uint32_t bkt[K], tag[K];
-      int res[K];
+    for (int k = 0; k < K; ++k) {
+      valid[k] = p0 + k < n;
+      const KeyHash kh = hash_from_h<G>(d, h[k]);
+      bkt[k] = kh.i1;
+      tag[k] = kh.fp;
+    }
+    if constexpr (OP == SOP_CONTAINS) {
+      Bucket<G> bk[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const uint32_t loc = uint32_t(r * K + k) * blockDim.x + threadIdx.x;
-        valid[k] = t0 + loc < n;
-        const KeyHash kh = hash_from_h<G>(d, hr[r * K + k]);
-        bkt[k] = kh.i1;
-        tag[k] = kh.fp;
+      for (int k = 0; k < K; ++k)
+        if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
+    } else {
+      cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
+    }
+    uint32_t slrk[K];  // slice << 16 | rank of a pending record, else kNoSlot
+    uint64_t fl = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      slrk[k] = kNoSlot;
+      uint32_t v = 0;
+      if (valid[k] && res[k] == TI_FULL) {
+        const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
+        slrk[k] = (sl << 16) | atomicAdd(&s_cnt[sl], 1u);
+        stash_h[me + k] = h[k];
+        v = kPending;
+      } else if (valid[k]) {
+        if (res[k] == TI_OK) {
+          v = 1;
+          c.ok++;
+        } else {
+          v = 2;
+          c.cont++;
+          if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
+        }
       }
-      if constexpr (OP == SOP_CONTAINS) {
-        Bucket<G> bk[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
+      fl |= uint64_t(v) << (8 * k);
+    }
+    if (want_flags) {
+      if (full && K == 8) {
+        st_cs_u64(reinterpret_cast<uint64_t*>(sb.f1 + p0), fl);
       } else {
-        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
-      }
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const uint32_t loc = uint32_t(r * K + k) * blockDim.x + threadIdx.x;
-        const bool pend = valid[k] && res[k] == TI_FULL;
-        // Stash slot: one shared atomic per warp.
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, pend);
-        uint32_t e0 = 0;
-        if (bal && lane == uint32_t(__ffs(bal) - 1)) e0 = atomicAdd(&s_n, uint32_t(__popc(bal)));
-        e0 = __shfl_sync(0xFFFFFFFFu, e0, __ffs(bal ? bal : 1u) - 1);
-        uint8_t v = 0;
-        if (pend) {
-          const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
-          const uint32_t rk = atomicAdd(&s_cnt[sl], 1u);
-          const uint32_t e = e0 + __popc(bal & ((1u << lane) - 1u));
-          stash_h[e] = hr[r * K + k];
-          stash_pk[e] = (sl << 22) | (rk << 11) | loc;
-          v = kPending;
-        } else if (valid[k]) {
-          if (res[k] == TI_OK) {
-            v = 1;
-            c.ok++;
-          } else {
-            v = 2;
-            c.cont++;
-            if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
-          }
-        }
-        if (valid[k] && want_flags) {
-          st_flag(sb.f1 + t0 + loc, v);
-          if (!pend) sb.link[t0 + loc] = 0u;
-        }
+        for (int k = 0; k < K; ++k)
+          if (valid[k]) st_flag(sb.f1 + p0 + k, uint8_t(fl >> (8 * k)));
       }
     }
     __syncthreads();
@@ -367,20 +381,36 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint64_t n, int want_flags) {
       s_spill[s] = room < cnt ? atomicAdd(&sb.fill2[S * kCtrStride], cnt - uint32_t(room))
                               : 0u;
     }
-    const uint32_t np = s_n;
-    for (uint32_t e = threadIdx.x; e < np; e += blockDim.x) {
-      const uint32_t pk = stash_pk[e];
-      s_order[s_off[pk >> 22] + ((pk >> 11) & 0x7FFu)] = uint16_t(e);
+    const uint32_t np = s_off[S - 1] + s_cnt[S - 1];
+    __syncthreads();
+    uint32_t lk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      lk[k] = 0;
+      if (slrk[k] != kNoSlot) {
+        const uint32_t sl = slrk[k] >> 16, rk = slrk[k] & 0xFFFFu;
+        s_order[s_off[sl] + rk] = (me + k) | (sl << 11);
+        lk[k] = uint32_t(rec2_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl], sb.cap2, S));
+      }
+    }
+    if (want_flags) {
+      if (full && K >= 4) {
+#pragma unroll
+        for (int k = 0; k < K; k += 4)
+          st_v4_u32(sb.link + p0 + k, lk[k], lk[k + 1], lk[k + 2], lk[k + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (valid[k]) sb.link[p0 + k] = lk[k];
+      }
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < np; j += blockDim.x) {
       const uint32_t e = s_order[j];
-      const uint32_t pk = stash_pk[e];
-      const uint32_t sl = pk >> 22;
+      const uint32_t sl = e >> 11;
       const uint64_t q = rec2_pos(sl, j - s_off[sl], s_base[sl], s_cnt[sl], s_spill[sl],
                                   sb.cap2, S);
-      sb.rec2[q] = stash_h[e];
-      if (want_flags) sb.link[t0 + (pk & 0x7FFu)] = uint32_t(q);
+      sb.rec2[q] = stash_h[e & 0x7FFu];
     }
     __syncthreads();
   }
@@ -422,26 +452,41 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
   block_scan_excl(s_len, s_start, NR, tmp);
   const uint64_t total = uint64_t(s_start[NR - 1]) + s_len[NR - 1];
   const uint32_t lane = threadIdx.x & 31;
-  const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
-  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const uint32_t T = blockDim.x * K;
+  __shared__ uint32_t s_tile;
+  uint32_t* tile_ctr = sb.fill2 + (S + 1) * kCtrStride;
   TileCounts c;
   const QueuePush push{&d.ctrl->queue_count, queue};
-  for (uint64_t base = gw * (32u * K); base < total; base += nw * (32u * K)) {
+  // The region (S slices, then the spill region) holding compacted
+  // position x: the last one starting at or before x.
+  auto region_of = [&](uint64_t x) {
+    uint32_t lo = 0, hi = NR;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_start[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+  };
+  // Block tiles of T compacted positions, handed out in order by a counter
+  // (see probe1); lane-strided inside the tile.
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const uint64_t x0 = uint64_t(s_tile) * T;
+    __syncthreads();
+    if (x0 >= total) break;
+    const uint64_t xl = (x0 + T < total ? x0 + T : total) - 1;
+    const uint32_t r0 = region_of(x0), r1 = region_of(xl);
     bool valid[K];
     uint64_t q[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const uint64_t x = base + uint64_t(k) * 32 + lane;
+      const uint64_t x = x0 + uint64_t(k) * blockDim.x + threadIdx.x;
       valid[k] = x < total;
       q[k] = 0;
       if (valid[k]) {
-        // The last region starting at or before x holds it.
-        uint32_t lo = 0, hi = NR;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (s_start[mid] <= x) lo = mid; else hi = mid;
-        }
-        q[k] = uint64_t(lo) * sb.cap2 + (x - s_start[lo]);
+        const uint32_t r = r0 == r1 ? r0 : region_of(x);
+        q[k] = uint64_t(r) * sb.cap2 + (x - s_start[r]);
       }
     }
     uint32_t bkt[K], tag[K];
@@ -603,12 +648,11 @@ struct SliceLaunch {
   static cudaError_t probes(const DevFilter& d, const SliceBufs& sb, uint64_t n,
                             int want, uint32_t* queue, cudaStream_t s,
                             KernelTimer* t) {
-    constexpr int R = 8 / K;  // tiles of kBlock * 8 records
-    constexpr uint32_t T = kBlock * K * R;
-    const size_t smem = size_t(14) * T + size_t(16) * sb.n_slices;
-    auto p1 = k_slice_probe1<G, OP, K, R>;
+    constexpr uint32_t T = kBlock * K;
+    const size_t smem = size_t(12) * T + size_t(16) * sb.n_slices;
+    auto p1 = k_slice_probe1<G, OP, K>;
     if (t) t->begin(KK_SLICE_PROBE1, s);
-    p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, n, want);
+    p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, uint32_t(n), want);
     if (t) t->end(KK_SLICE_PROBE1, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -49,6 +49,7 @@ struct DevFilter {
 };
 
 constexpr uint32_t kSliceMax = 1024;  // slices per table (shared-memory bins)
+constexpr uint32_t kFill2Extra = 3;   // counters after the S per-slice ones
 
 // Device scratch of the slice-partitioned path for chunks of up to n keys
 // (see cf_slice.cuh).
@@ -57,7 +58,8 @@ struct SliceBufs {
   uint32_t shift;     // slice of bucket j = j >> shift
   uint64_t cap2;      // rec2 records per slice (the spill region follows)
   uint32_t* cursor;   // [S * 32] histogram, then scatter cursors (one per line)
-  uint32_t* fill2;    // [(S + 1) * 32] rec2 records claimed per slice; slice S = spill
+  uint32_t* fill2;    // [(S + 3) * 32] rec2 records claimed per slice, then
+                      // the spill count and two tile counters
   uint32_t* dst;      // [n]     rec1 position of key j
   uint64_t* rec1;     // [n]     key hashes grouped by the slice of i1
   uint8_t* f1;        // [n]     result of probe1 (kPending: see link / f2)
