@@ -31,6 +31,11 @@ constexpr int kBlock = 256;
 #ifndef CF_MINB_MUT
 #define CF_MINB_MUT 2
 #endif
+// Minimum resident blocks per SM requested for the eviction kernel (its
+// chains are latency-bound: more resident warps, more chains in flight).
+#ifndef CF_MINB_EVICT
+#define CF_MINB_EVICT 1
+#endif
 // BFS frontier width of the single-filter eviction kernel: the number of
 // candidates whose alternate buckets are loaded together (CF_EVICT_FW; 0 or
 // an invalid value means b/2, all at once).
@@ -457,7 +462,7 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
 // FROM_HASH: keys[] holds the keys' 64-bit hashes instead of the keys (the
 // slice-partitioned path queues positions of its hash records).
 template <class G, bool FROM_HASH = false>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, CF_MINB_EVICT)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
                uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
                const uint32_t* __restrict__ queue) {
@@ -654,6 +659,19 @@ inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
   return unsigned(need < cap ? need : cap);
 }
 
+// Grid of the eviction kernel: CF_EVICT_BPSM blocks per SM (0: as many as
+// fit).  Its chains are bound by the DRAM random-access rate, and more
+// chains in flight only add queueing (2^28-bucket workload, eviction ms per
+// step at 1 / 2 / 3 / 4 / 5 blocks per SM: 65.6 / 61.2 / 62.5 / 63.2 / 68.8).
+#ifndef CF_EVICT_BPSM
+#define CF_EVICT_BPSM 2
+#endif
+inline unsigned evict_grid(const void* fn) {
+  const int occ = cached_occupancy(fn, kBlock);
+  const int per = CF_EVICT_BPSM > 0 && CF_EVICT_BPSM < occ ? CF_EVICT_BPSM : occ;
+  return unsigned(device_sm_count() * (per > 0 ? per : 1));
+}
+
 // Optional per-launch timing: the host side records CUDA events around each
 // kernel launch on the launching stream (cf_set_kernel_timing).
 enum KernelKind : int {
@@ -708,9 +726,8 @@ struct Launch {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto f2 = k_insert_evict<G>;
-    const int occ = cached_occupancy(reinterpret_cast<const void*>(f2), kBlock);
     if (t) t->begin(KK_INSERT_EVICT, s);
-    f2<<<unsigned(device_sm_count() * (occ > 0 ? occ : 1)), kBlock, 0, s>>>(
+    f2<<<evict_grid(reinterpret_cast<const void*>(f2)), kBlock, 0, s>>>(
         d, keys, flags, evout, queue);
     if (t) t->end(KK_INSERT_EVICT, s);
     return cudaGetLastError();

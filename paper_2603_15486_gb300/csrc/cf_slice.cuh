@@ -62,6 +62,17 @@ __device__ __forceinline__ uint32_t ld_cs_u32(const uint32_t* p) {
   asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
+__device__ __forceinline__ void ld_cs_v2_u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.global.cs.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+__device__ __forceinline__ void st_v4_u32(uint32_t* p, uint32_t a, uint32_t b, uint32_t c,
+                                          uint32_t e) {
+  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
+               "r"(e));
+}
+__device__ __forceinline__ void st_cs_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
 
 // ---------------------------------------------------------------------------
 // hist: counts of i1's slice.  Each block bins its keys in shared memory and
@@ -265,17 +276,6 @@ __device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
 // rec2 as one run per occupied slice (one claim on fill2 per run).
 // Shared memory: 12*T bytes + 4*S counters (T = kBlock*K <= 2048).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ld_cs_v2_u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
-  asm volatile("ld.global.cs.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
-}
-__device__ __forceinline__ void st_v4_u32(uint32_t* p, uint32_t a, uint32_t b, uint32_t c,
-                                          uint32_t e) {
-  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
-               "r"(e));
-}
-__device__ __forceinline__ void st_cs_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v));
-}
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
@@ -696,9 +696,8 @@ struct SliceLaunch {
     if (e != cudaSuccess) return e;
     if (op == SOP_INSERT) {
       auto fe = k_insert_evict<G, true>;
-      const int occ = cached_occupancy(reinterpret_cast<const void*>(fe), kBlock);
       if (t) t->begin(KK_INSERT_EVICT, s);
-      fe<<<unsigned(device_sm_count() * (occ > 0 ? occ : 1)), kBlock, 0, s>>>(
+      fe<<<evict_grid(reinterpret_cast<const void*>(fe)), kBlock, 0, s>>>(
           d, sb.rec2, want ? sb.f2 : nullptr, nullptr, queue);
       if (t) t->end(KK_INSERT_EVICT, s);
       e = cudaGetLastError();
