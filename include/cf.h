@@ -104,7 +104,9 @@ typedef struct {
                               new tag in first, so nothing is ever undone) */
   uint64_t rollback_lost;  /* always 0, as rollbacks                        */
   uint64_t contention;     /* bounded CAS loops that ran out                */
-  uint32_t error_word;     /* bit 0: contention; bit 1: victim log full     */
+  uint32_t error_word;     /* bit 0: contention; bit 1: victim log full;
+                              bit 2: an asynchronous copy of the sliced
+                              path timed out (its records were skipped)    */
   uint32_t victim_capacity;
 } cf_stats_t;
 

@@ -75,6 +75,48 @@ __device__ __forceinline__ void st_cs_u64(uint64_t* p, uint64_t v) {
 }
 
 // ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) from global to shared memory
+// completing on an mbarrier, with bounded waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One thread: expect `bytes` and start the copy of `bytes` (a multiple of 16,
+// both addresses 16-byte aligned) from global src to shared dst.  bytes == 0
+// only arrives, which completes the phase at once.
+__device__ __forceinline__ void bulk_load(uint64_t* bar, void* dst, const void* src,
+                                          uint32_t bytes) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  if (bytes)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Wait for the phase with the given parity to complete; false if it has not
+// after a bounded number of polls (the caller reports the timeout).
+constexpr uint32_t kMaxMbarPolls = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kMaxMbarPolls; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+constexpr uint32_t kErrAsyncCopy = 4u;  // error_word bit: a bulk copy never completed
+
+// ---------------------------------------------------------------------------
 // hist: counts of i1's slice.  Each block bins its keys in shared memory and
 // adds its bins to the global histogram once.
 // ---------------------------------------------------------------------------
@@ -269,12 +311,12 @@ __device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
 
 // ---------------------------------------------------------------------------
 // probe1: the operation on bucket i1 for rec1 records in order.  A block
-// tile is kBlock*K records, thread t owning the K consecutive records
-// t*K .. t*K+K-1 (vector loads of rec1, one 8-byte store of their flags, two
-// 16-byte stores of their links).  Records left pending are stashed in
-// shared memory, sorted by the slice of i2 once per tile, and written to
-// rec2 as one run per occupied slice (one claim on fill2 per run).
-// Shared memory: 12*T bytes + 4*S counters (T = kBlock*K <= 2048).
+// tile is kBlock*K records (thread t takes records t, t + kBlock, ...),
+// staged in shared memory by a TMA bulk copy issued while the block works
+// on the previous tile.  Records left pending are stashed in shared memory,
+// sorted by the slice of i2 once per tile, and written to rec2 as one run
+// per occupied slice (one claim on fill2 per run).
+// Shared memory: 20*T bytes + 4*S counters (T = kBlock*K <= 2048).
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
@@ -287,42 +329,68 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
   static_assert(T <= 2048, "shared entries pack an 11-bit tile index");
   extern __shared__ uint64_t sm64[];
   const uint32_t S = sb.n_slices;
-  uint64_t* stash_h = sm64;                                     // [T] by tile index
-  uint32_t* s_order = reinterpret_cast<uint32_t*>(sm64 + T);   // [T] index | slice << 11
-  uint32_t* s_cnt = s_order + T;                                // [S]
-  uint32_t* s_off = s_cnt + S;                                  // [S]
-  uint32_t* s_base = s_off + S;                                 // [S]
-  uint32_t* s_spill = s_base + S;                               // [S]
+  uint64_t* pref = sm64;                                            // [T] next tile's records
+  uint64_t* stash_h = sm64 + T;                                     // [T] by tile index
+  uint32_t* s_order = reinterpret_cast<uint32_t*>(sm64 + 2 * T);   // [T] index | slice << 11
+  uint32_t* s_cnt = s_order + T;                                    // [S]
+  uint32_t* s_off = s_cnt + S;                                      // [S]
+  uint32_t* s_base = s_off + S;                                     // [S]
+  uint32_t* s_spill = s_base + S;                                   // [S]
   __shared__ uint32_t tmp[32];
-  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_next;
+  __shared__ __align__(8) uint64_t s_bar;
   TileCounts c;
-  const uint32_t me = threadIdx.x * K;  // first tile index of this thread
   // Tiles are handed out in order by a counter, so the blocks at work stay
   // within a window of consecutive tiles (one or two slices) instead of
-  // drifting apart as a static grid stride lets them.
+  // drifting apart as a static grid stride lets them.  One thread copies the
+  // next tile's records into shared memory (TMA bulk copy) while the block
+  // works on the current one.
   uint32_t* tile_ctr = sb.fill2 + (S + 2) * kCtrStride;
+  auto tile_bytes = [&](uint32_t tile) -> uint32_t {
+    const uint32_t t0 = tile * T;
+    return t0 >= n ? 0u : ((n - t0 < T ? n - t0 : T) * 8u) & ~15u;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    s_next = atomicAdd(tile_ctr, 1u);
+    if (s_next * T < n) bulk_load(&s_bar, pref, sb.rec1 + size_t(s_next) * T, tile_bytes(s_next));
+  }
+  __syncthreads();
+  uint32_t tile = s_next;
+  uint32_t parity = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
-    __syncthreads();
-    const uint32_t t0 = s_tile * T;
+    const uint32_t t0 = tile * T;
     if (t0 >= n) break;
-    const uint32_t p0 = t0 + me;
-    const bool full = p0 + K <= n;
-    uint64_t h[K];
-    if (full && K % 2 == 0) {
-#pragma unroll
-      for (int k = 0; k + 1 < K; k += 2) ld_cs_v2_u64(sb.rec1 + p0 + k, h[k], h[k + 1]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < K; ++k) h[k] = p0 + k < n ? ld_stream_u64(sb.rec1 + p0 + k) : 0ull;
+    if (!mbar_wait(&s_bar, parity)) {
+      // The copy did not complete: report it and leave this tile (its
+      // records stay unprocessed; the error bit tells the caller).
+      if (threadIdx.x == 0) atomicOr(&d.ctrl->error_word, kErrAsyncCopy);
+      mbar_wait(&s_bar, parity);  // once more (bounded) for the copy in flight
+      break;
     }
+    parity ^= 1u;
+    // Record k of this thread: tile index loc(k) = k*kBlock + thread (lane-
+    // strided: conflict-free reads of the staged tile, coalesced stores).
+    const uint32_t copied = tile_bytes(tile) / 8u;  // records now in pref
+    uint64_t h[K];
     bool valid[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t loc = uint32_t(k) * kBlock + threadIdx.x;
+      valid[k] = t0 + loc < n;
+      h[k] = loc < copied ? pref[loc] : (valid[k] ? ld_stream_u64(sb.rec1 + t0 + loc) : 0ull);
+    }
+    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
+    __syncthreads();  // pref consumed, counters zeroed
+    if (threadIdx.x == 0) {
+      s_next = atomicAdd(tile_ctr, 1u);
+      if (s_next * T < n)
+        bulk_load(&s_bar, pref, sb.rec1 + size_t(s_next) * T, tile_bytes(s_next));
+    }
     uint32_t bkt[K], tag[K];
     int res[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      valid[k] = p0 + k < n;
       const KeyHash kh = hash_from_h<G>(d, h[k]);
       bkt[k] = kh.i1;
       tag[k] = kh.fp;
@@ -339,15 +407,15 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
       cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
     }
     uint32_t slrk[K];  // slice << 16 | rank of a pending record, else kNoSlot
-    uint64_t fl = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+      const uint32_t loc = uint32_t(k) * kBlock + threadIdx.x;
       slrk[k] = kNoSlot;
-      uint32_t v = 0;
+      uint8_t v = 0;
       if (valid[k] && res[k] == TI_FULL) {
         const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
         slrk[k] = (sl << 16) | atomicAdd(&s_cnt[sl], 1u);
-        stash_h[me + k] = h[k];
+        stash_h[loc] = h[k];
         v = kPending;
       } else if (valid[k]) {
         if (res[k] == TI_OK) {
@@ -359,16 +427,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
           if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
         }
       }
-      fl |= uint64_t(v) << (8 * k);
-    }
-    if (want_flags) {
-      if (full && K == 8) {
-        st_cs_u64(reinterpret_cast<uint64_t*>(sb.f1 + p0), fl);
-      } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if (valid[k]) st_flag(sb.f1 + p0 + k, uint8_t(fl >> (8 * k)));
-      }
+      if (want_flags && valid[k]) st_flag(sb.f1 + t0 + loc, v);
     }
     __syncthreads();
     block_scan_excl(s_cnt, s_off, S, tmp);
@@ -383,26 +442,16 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
     }
     const uint32_t np = s_off[S - 1] + s_cnt[S - 1];
     __syncthreads();
-    uint32_t lk[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      lk[k] = 0;
+      const uint32_t loc = uint32_t(k) * kBlock + threadIdx.x;
+      uint32_t lk = 0;
       if (slrk[k] != kNoSlot) {
         const uint32_t sl = slrk[k] >> 16, rk = slrk[k] & 0xFFFFu;
-        s_order[s_off[sl] + rk] = (me + k) | (sl << 11);
-        lk[k] = uint32_t(rec2_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl], sb.cap2, S));
+        s_order[s_off[sl] + rk] = loc | (sl << 11);
+        lk = uint32_t(rec2_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl], sb.cap2, S));
       }
-    }
-    if (want_flags) {
-      if (full && K >= 4) {
-#pragma unroll
-        for (int k = 0; k < K; k += 4)
-          st_v4_u32(sb.link + p0 + k, lk[k], lk[k + 1], lk[k + 2], lk[k + 3]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if (valid[k]) sb.link[p0 + k] = lk[k];
-      }
+      if (want_flags && valid[k]) sb.link[t0 + loc] = lk;
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < np; j += blockDim.x) {
@@ -413,6 +462,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
       sb.rec2[q] = stash_h[e & 0x7FFu];
     }
     __syncthreads();
+    tile = s_next;
   }
   if constexpr (OP == SOP_INSERT) {
     block_add(&d.ctrl->occupancy, c.ok);
@@ -649,8 +699,13 @@ struct SliceLaunch {
                             int want, uint32_t* queue, cudaStream_t s,
                             KernelTimer* t) {
     constexpr uint32_t T = kBlock * K;
-    const size_t smem = size_t(12) * T + size_t(16) * sb.n_slices;
+    const size_t smem = size_t(20) * T + size_t(16) * sb.n_slices;
     auto p1 = k_slice_probe1<G, OP, K>;
+    if (smem > 48 * 1024) {
+      const cudaError_t ea =
+          cudaFuncSetAttribute(p1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (ea != cudaSuccess) return ea;
+    }
     if (t) t->begin(KK_SLICE_PROBE1, s);
     p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, uint32_t(n), want);
     if (t) t->end(KK_SLICE_PROBE1, s);

@@ -58,6 +58,7 @@ def test_sliced_query_bit_exact(cf, f, b, policy):
     got = g.contains(to_dev(q)).cpu().numpy()
     assert _ran_sliced(g)
     assert np.array_equal(got, o.contains_batch(q))
+    assert g.stats()["error_word"] == 0
     assert np.array_equal(g.snapshot(), o.snapshot())      # a query writes nothing
     g.set_slicing("off")
     assert np.array_equal(g.contains(to_dev(q)).cpu().numpy(), got)
