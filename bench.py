@@ -36,6 +36,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "insert/query/delete Mops/s at LF 0.95 vs HBM roofline; served p99 vs plain"
+
+# DRAM bytes (read + write) per launch of the filter kernels on the large
+# workload, from one ncu capture of the current kernels (1 pass: the metrics
+# dram__bytes_read.sum and dram__bytes_write.sum over the timed step of
+# `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu`; its summary and command
+# are committed with the other ncu summaries).  Must be re-taken whenever one
+# of these kernels changes.
+NCU_DRAM_BYTES_PER_LAUNCH = {"insert_evict": 162.282e9 / 5}
 SECTOR = 32
 
 
@@ -414,7 +422,11 @@ def gpu_arm(args):
     ceiling = random_gather_ceiling(stream)
     out["roofline"] = {"bound": "hbm", "kernel": dom,
                        "achieved": kern[dom]["achieved_GBps"], "peak": peak, "unit": "GB/s",
-                       "frac": kern[dom]["frac"], "traffic": args.traffic,
+                       "frac": kern[dom]["frac"],
+                       "traffic": (args.traffic if args.traffic is not None
+                                   else NCU_DRAM_BYTES_PER_LAUNCH.get(dom)
+                                   if (W.name, args.slicing) == ("large_2^28x4_f16_lf0.95", "auto")
+                                   else None),
                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
                        if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
                        "random_sector_ceiling_GBps": ceiling["GBps_32B"],
@@ -940,7 +952,8 @@ def main(argv=None):
     ap.add_argument("--slice-chunk", type=int, default=0,
                     help="keys per sliced pass (0: the library default, 2^28)")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture "
+                         "(default: the committed full-size capture of the eviction loop)")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1")
