@@ -799,6 +799,7 @@ def ablation_arm(args):
     evict = {}
     for pol in ("bfs", "dfs"):
         g = CuckooFilter(m, 16, b, 500, eviction=pol)
+        g.set_slicing(args.slicing, args.slice_bytes, args.slice_chunk)
         rows = {}
         for alpha in (0.75, 0.8, 0.85, 0.9, 0.95, 0.98, 1.0):
             n = workloads.lf_count(m, b, alpha)
@@ -834,6 +835,7 @@ def ablation_arm(args):
         res = {}
         for pol in ("xor", "offset"):
             g = CuckooFilter(mm, 16, b, 500, policy=pol)
+            g.set_slicing(args.slicing, args.slice_bytes, args.slice_chunk)
 
             def ins(phase, g=g):
                 if phase == "pre":
@@ -868,7 +870,7 @@ def ablation_arm(args):
             "higher_is_better": True,
             "config": {"geometry": "f16, b = 16", "eviction_table": "2^28 slots (2^24 buckets)",
                        "eviction_protocol": "pre-fill 3/4 of the target load, time the last 1/4",
-                       "policy_load_factor": 0.95},
+                       "policy_load_factor": 0.95, "slicing": args.slicing},
             "eviction": evict, "bucket_policy": policy}
 
 

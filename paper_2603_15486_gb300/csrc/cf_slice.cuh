@@ -311,7 +311,7 @@ __device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
 
 // ---------------------------------------------------------------------------
 // probe1: the operation on bucket i1 for rec1 records in order.  A block
-// tile is kBlock*K records (thread t takes records t, t + kBlock, ...),
+// tile is kBlock*8 records (thread t takes records t, t + kBlock, ...),
 // staged in shared memory by a TMA bulk copy issued while the block works
 // on the previous tile.  Records left pending are stashed in shared memory,
 // sorted by the slice of i2 once per tile, and written to rec2 as one run
@@ -324,7 +324,12 @@ constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 template <class G, int OP, int K>
 __global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
 k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
-  constexpr uint32_t T = kBlock * K;
+  // R rounds of K records per thread: every tile holds 8 records per thread
+  // whatever the bucket size (K = 8 / 4 / 2 / 1 for 8 / 16 / 32 / 64-byte
+  // buckets), so the per-tile work (barriers, prefix, claims) stays amortised.
+  constexpr int R = 8 / K;
+  constexpr int N = R * K;
+  constexpr uint32_t T = kBlock * N;
   static_assert(K == 8 || K == 4 || K == 2 || K == 1, "records per thread");
   static_assert(T <= 2048, "shared entries pack an 11-bit tile index");
   extern __shared__ uint64_t sm64[];
@@ -369,16 +374,16 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
       break;
     }
     parity ^= 1u;
-    // Record k of this thread: tile index loc(k) = k*kBlock + thread (lane-
+    // Record i of this thread: tile index loc(i) = i*kBlock + thread (lane-
     // strided: conflict-free reads of the staged tile, coalesced stores).
     const uint32_t copied = tile_bytes(tile) / 8u;  // records now in pref
-    uint64_t h[K];
-    bool valid[K];
+    uint64_t hr[N];
+    bool vr[N];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint32_t loc = uint32_t(k) * kBlock + threadIdx.x;
-      valid[k] = t0 + loc < n;
-      h[k] = loc < copied ? pref[loc] : (valid[k] ? ld_stream_u64(sb.rec1 + t0 + loc) : 0ull);
+    for (int i = 0; i < N; ++i) {
+      const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
+      vr[i] = t0 + loc < n;
+      hr[i] = loc < copied ? pref[loc] : (vr[i] ? ld_stream_u64(sb.rec1 + t0 + loc) : 0ull);
     }
     for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
     __syncthreads();  // pref consumed, counters zeroed
@@ -387,47 +392,53 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
       if (s_next * T < n)
         bulk_load(&s_bar, pref, sb.rec1 + size_t(s_next) * T, tile_bytes(s_next));
     }
-    uint32_t bkt[K], tag[K];
-    int res[K];
+    uint32_t slrk[N];  // slice << 16 | rank of a pending record, else kNoSlot
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const KeyHash kh = hash_from_h<G>(d, h[k]);
-      bkt[k] = kh.i1;
-      tag[k] = kh.fp;
-    }
-    if constexpr (OP == SOP_CONTAINS) {
-      Bucket<G> bk[K];
+    for (int r = 0; r < R; ++r) {
+      bool valid[K];
+      uint32_t bkt[K], tag[K];
+      int res[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
-    } else {
-      cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
-    }
-    uint32_t slrk[K];  // slice << 16 | rank of a pending record, else kNoSlot
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint32_t loc = uint32_t(k) * kBlock + threadIdx.x;
-      slrk[k] = kNoSlot;
-      uint8_t v = 0;
-      if (valid[k] && res[k] == TI_FULL) {
-        const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
-        slrk[k] = (sl << 16) | atomicAdd(&s_cnt[sl], 1u);
-        stash_h[loc] = h[k];
-        v = kPending;
-      } else if (valid[k]) {
-        if (res[k] == TI_OK) {
-          v = 1;
-          c.ok++;
-        } else {
-          v = 2;
-          c.cont++;
-          if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
-        }
+      for (int k = 0; k < K; ++k) {
+        valid[k] = vr[r * K + k];
+        const KeyHash kh = hash_from_h<G>(d, hr[r * K + k]);
+        bkt[k] = kh.i1;
+        tag[k] = kh.fp;
       }
-      if (want_flags && valid[k]) st_flag(sb.f1 + t0 + loc, v);
+      if constexpr (OP == SOP_CONTAINS) {
+        Bucket<G> bk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
+      } else {
+        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int i = r * K + k;
+        const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
+        slrk[i] = kNoSlot;
+        uint8_t v = 0;
+        if (valid[k] && res[k] == TI_FULL) {
+          const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
+          slrk[i] = (sl << 16) | atomicAdd(&s_cnt[sl], 1u);
+          stash_h[loc] = hr[i];
+          v = kPending;
+        } else if (valid[k]) {
+          if (res[k] == TI_OK) {
+            v = 1;
+            c.ok++;
+          } else {
+            v = 2;
+            c.cont++;
+            if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
+          }
+        }
+        if (want_flags && valid[k]) st_flag(sb.f1 + t0 + loc, v);
+      }
     }
     __syncthreads();
     block_scan_excl(s_cnt, s_off, S, tmp);
@@ -443,15 +454,15 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
     const uint32_t np = s_off[S - 1] + s_cnt[S - 1];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint32_t loc = uint32_t(k) * kBlock + threadIdx.x;
+    for (int i = 0; i < N; ++i) {
+      const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
       uint32_t lk = 0;
-      if (slrk[k] != kNoSlot) {
-        const uint32_t sl = slrk[k] >> 16, rk = slrk[k] & 0xFFFFu;
+      if (slrk[i] != kNoSlot) {
+        const uint32_t sl = slrk[i] >> 16, rk = slrk[i] & 0xFFFFu;
         s_order[s_off[sl] + rk] = loc | (sl << 11);
         lk = uint32_t(rec2_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl], sb.cap2, S));
       }
-      if (want_flags && valid[k]) sb.link[t0 + loc] = lk;
+      if (want_flags && vr[i]) sb.link[t0 + loc] = lk;
     }
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < np; j += blockDim.x) {
@@ -502,7 +513,10 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
   block_scan_excl(s_len, s_start, NR, tmp);
   const uint64_t total = uint64_t(s_start[NR - 1]) + s_len[NR - 1];
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t T = blockDim.x * K;
+  // R rounds of K positions per thread: tiles of 8 records per thread for
+  // every bucket size (see probe1).
+  constexpr int R = 8 / K;
+  const uint32_t T = blockDim.x * K * R;
   __shared__ uint32_t s_tile;
   uint32_t* tile_ctr = sb.fill2 + (S + 1) * kCtrStride;
   TileCounts c;
@@ -527,62 +541,65 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
     if (x0 >= total) break;
     const uint64_t xl = (x0 + T < total ? x0 + T : total) - 1;
     const uint32_t r0 = region_of(x0), r1 = region_of(xl);
-    bool valid[K];
-    uint64_t q[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t x = x0 + uint64_t(k) * blockDim.x + threadIdx.x;
-      valid[k] = x < total;
-      q[k] = 0;
-      if (valid[k]) {
-        const uint32_t r = r0 == r1 ? r0 : region_of(x);
-        q[k] = uint64_t(r) * sb.cap2 + (x - s_start[r]);
-      }
-    }
-    uint32_t bkt[K], tag[K];
-    int r[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const KeyHash kh =
-          hash_from_h<G>(d, valid[k] ? ld_stream_u64(sb.rec2 + q[k]) : 0ull);
-      bkt[k] = alt_index<G>(d, kh.i1, kh.fp);
-      tag[k] = kh.fp | G::kChoice;
-    }
-    if constexpr (OP == SOP_CONTAINS) {
-      Bucket<G> bk[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        if (valid[k] && want_flags)
-          st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
-    } else {
-      cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, r);
-      bool to_queue[K];
-      uint32_t qidx[K];
+    for (int rr = 0; rr < R; ++rr) {
+      bool valid[K];
+      uint64_t q[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        to_queue[k] = false;
-        qidx[k] = uint32_t(q[k]);
+        const uint64_t x = x0 + uint64_t(rr * K + k) * blockDim.x + threadIdx.x;
+        valid[k] = x < total;
+        q[k] = 0;
         if (valid[k]) {
-          uint8_t v;
-          if (r[k] == TI_OK) {
-            v = 1;
-            c.ok++;
-          } else if (r[k] == TI_CONTENTION) {
-            v = 2;
-            c.cont++;
-            if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
-          } else {
-            v = 0;
-            if (OP == SOP_INSERT) to_queue[k] = true;
-            else c.fail++;
-          }
-          if (want_flags && !to_queue[k]) st_flag(sb.f2 + q[k], v);
+          const uint32_t r = r0 == r1 ? r0 : region_of(x);
+          q[k] = uint64_t(r) * sb.cap2 + (x - s_start[r]);
         }
       }
-      if constexpr (OP == SOP_INSERT) push.push_all(to_queue, qidx, lane);
+      uint32_t bkt[K], tag[K];
+      int res[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const KeyHash kh =
+            hash_from_h<G>(d, valid[k] ? ld_stream_u64(sb.rec2 + q[k]) : 0ull);
+        bkt[k] = alt_index<G>(d, kh.i1, kh.fp);
+        tag[k] = kh.fp | G::kChoice;
+      }
+      if constexpr (OP == SOP_CONTAINS) {
+        Bucket<G> bk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (valid[k]) bk[k] = load_bucket<G, false>(bucket_ptr<G>(d, bkt[k]));
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (valid[k] && want_flags)
+            st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
+      } else {
+        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
+        bool to_queue[K];
+        uint32_t qidx[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          to_queue[k] = false;
+          qidx[k] = uint32_t(q[k]);
+          if (valid[k]) {
+            uint8_t v;
+            if (res[k] == TI_OK) {
+              v = 1;
+              c.ok++;
+            } else if (res[k] == TI_CONTENTION) {
+              v = 2;
+              c.cont++;
+              if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
+            } else {
+              v = 0;
+              if (OP == SOP_INSERT) to_queue[k] = true;
+              else c.fail++;
+            }
+            if (want_flags && !to_queue[k]) st_flag(sb.f2 + q[k], v);
+          }
+        }
+        if constexpr (OP == SOP_INSERT) push.push_all(to_queue, qidx, lane);
+      }
     }
   }
   if constexpr (OP == SOP_INSERT) {
@@ -698,7 +715,7 @@ struct SliceLaunch {
   static cudaError_t probes(const DevFilter& d, const SliceBufs& sb, uint64_t n,
                             int want, uint32_t* queue, cudaStream_t s,
                             KernelTimer* t) {
-    constexpr uint32_t T = kBlock * K;
+    constexpr uint32_t T = kBlock * 8;
     const size_t smem = size_t(20) * T + size_t(16) * sb.n_slices;
     auto p1 = k_slice_probe1<G, OP, K>;
     if (smem > 48 * 1024) {
@@ -714,7 +731,7 @@ struct SliceLaunch {
     auto p2 = k_slice_probe2<G, OP, K>;
     const size_t smem2 = size_t(2) * (sb.n_slices + 1) * sizeof(uint32_t);
     if (t) t->begin(KK_SLICE_PROBE2, s);
-    p2<<<persistent_grid(p2, n, kBlock * K), kBlock, smem2, s>>>(d, sb, n, want, queue);
+    p2<<<persistent_grid(p2, n, kBlock * 8), kBlock, smem2, s>>>(d, sb, n, want, queue);
     if (t) t->end(KK_SLICE_PROBE2, s);
     return cudaGetLastError();
   }
