@@ -945,7 +945,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-warmup", type=int, default=1)
-    ap.add_argument("--e2e-chunk", type=int, default=1 << 26,
+    ap.add_argument("--e2e-chunk", type=int, default=1 << 25,
                     help="keys per staging chunk of the host-buffer calls")
     ap.add_argument("--slicing", choices=["off", "auto", "always"], default="auto",
                     help="slice-partitioned execution of the filter calls (cf_set_slicing)")

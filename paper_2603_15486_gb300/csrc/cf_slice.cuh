@@ -628,10 +628,13 @@ __device__ __forceinline__ uint32_t pending_mask(uint32_t w) {
   return m;
 }
 
+#ifndef CF_MERGE_V
+#define CF_MERGE_V 4
+#endif
 static __global__ void __launch_bounds__(kBlock)
 k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
               const uint8_t* __restrict__ f2, uint64_t n) {
-  constexpr int V = 4;
+  constexpr int V = CF_MERGE_V;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t n4 = n / 4;
   uint32_t* f1w = reinterpret_cast<uint32_t*>(f1);
@@ -672,7 +675,7 @@ k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
 static __global__ void __launch_bounds__(kBlock)
 k_slice_out(const uint32_t* __restrict__ dst, const uint8_t* __restrict__ f1,
             uint8_t* __restrict__ out, uint64_t n) {
-  constexpr int V = 4;
+  constexpr int V = CF_MERGE_V;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t n4 = n / 4;
   const bool aligned = (reinterpret_cast<uintptr_t>(out) & 3u) == 0;
@@ -777,9 +780,9 @@ struct SliceLaunch {
     }
     if (!want) return cudaSuccess;
     if (t) t->begin(KK_SLICE_MERGE, s);
-    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 16), kBlock, 0, s>>>(
-        sb.f1, sb.link, sb.f2, n);
-    k_slice_out<<<persistent_grid(k_slice_out, n, kBlock * 16), kBlock, 0, s>>>(
+    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 4 * CF_MERGE_V), kBlock, 0,
+                    s>>>(sb.f1, sb.link, sb.f2, n);
+    k_slice_out<<<persistent_grid(k_slice_out, n, kBlock * 4 * CF_MERGE_V), kBlock, 0, s>>>(
         sb.dst, sb.f1, flags, n);
     if (t) t->end(KK_SLICE_MERGE, s);
     return cudaGetLastError();
