@@ -62,17 +62,6 @@ __device__ __forceinline__ uint32_t ld_cs_u32(const uint32_t* p) {
   asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
-__device__ __forceinline__ void ld_cs_v2_u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
-  asm volatile("ld.global.cs.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
-}
-__device__ __forceinline__ void st_v4_u32(uint32_t* p, uint32_t a, uint32_t b, uint32_t c,
-                                          uint32_t e) {
-  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
-               "r"(e));
-}
-__device__ __forceinline__ void st_cs_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(v));
-}
 
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (TMA, cp.async.bulk) from global to shared memory
