@@ -243,11 +243,6 @@ def bytes_per_op(phases: dict, bucket_bytes: int) -> dict:
 # ---------------------------------------------------------------------------
 # GPU arm.
 # ---------------------------------------------------------------------------
-def insert_launches(n: int) -> int:
-    chunk = 1 << 28
-    return 2 * ((n + chunk - 1) // chunk)
-
-
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -280,7 +275,6 @@ def gpu_arm(args):
     stream.synchronize()
 
     segs = W.insert_segments()
-    launches = sum(insert_launches(hi - lo) for lo, hi in segs) + 2
 
     def step(ev=None):
         filt.clear(stream=stream)
@@ -374,7 +368,10 @@ def gpu_arm(args):
                    for k, v, n in (("insert", med["insert"], W.n_insert),
                                    ("query", med["query"], W.n_queries),
                                    ("delete", med["delete"], W.n_deletes))},
-        "gpu_launches": launches * args.steps,
+        # Kernels launched in the timed steps, from the per-kernel timer (one
+        # timer record covers hist + scan + scatter, and merge + out).
+        "gpu_launches": sum(n_l * {"slice_split": 3, "slice_merge": 2}.get(k, 1)
+                            for k, (n_l, _) in ktimes.items()),
         "checks": {"insert_ok": ins_ok, "insert_fail": W.n_insert - ins_ok,
                    "query_pos_found": q_pos, "query_pos": W.n_queries // 2,
                    "false_positives": q_neg, "fpr": q_neg / (W.n_queries // 2),
