@@ -134,10 +134,10 @@ def test_batched_mixed_ops_and_graph_replay_with_new_items(cf):
     A = [cf.CuckooFilter(m, f, b, 500) for _ in range(3)]
     ks = [workloads.keys(600 + i, 12000) for i in range(3)]
     bt = cf.Batch(8, 1 << 20)
-    # Round 1: insert into all three (graph captured here).
+    # First batch: insert into all three (graph captured here).
     bt.set([(A[i], "insert", to_dev(ks[i]), None) for i in range(3)])
     bt.launch(graph=True)
-    # Round 2, same graph replayed: query A0, remove half of A1, insert more into A2.
+    # Second batch, same graph replayed: query A0, remove half of A1, insert more into A2.
     out0 = torch.empty(ks[0].size, dtype=torch.uint8, device="cuda")
     rm1 = torch.empty(6000, dtype=torch.uint8, device="cuda")
     more = workloads.keys(603, 2000)
