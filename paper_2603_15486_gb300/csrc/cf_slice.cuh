@@ -65,9 +65,14 @@ enum : int { SOP_INSERT = 0, SOP_CONTAINS = 1, SOP_REMOVE = 2 };
 #ifndef CF_SLICE_MINB
 #define CF_SLICE_MINB 3
 #endif
-// Minimum resident blocks per SM of the split kernels (hist, scatter).
+#ifndef CF_SLICE2_MINB
+#define CF_SLICE2_MINB CF_SLICE_MINB
+#endif
+// Minimum resident blocks per SM of the split kernels (hist, scatter): 4
+// (64 registers) ran the split in 17.4 ms per step against 18.1 at the
+// compiler's own choice.
 #ifndef CF_SPLIT_MINB
-#define CF_SPLIT_MINB 1
+#define CF_SPLIT_MINB 4
 #endif
 
 __device__ __forceinline__ void st_cs_u32(uint32_t* p, uint32_t v) {
@@ -499,7 +504,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
 // past a region's fill are skipped.
 // ---------------------------------------------------------------------------
 template <class G, int OP, int K>
-__global__ void __launch_bounds__(kBlock, CF_SLICE_MINB)
+__global__ void __launch_bounds__(kBlock, CF_SLICE2_MINB)
 k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
                uint32_t* __restrict__ queue) {
   // The filled part of each region (S slices, then the spill region) and
@@ -636,7 +641,13 @@ __device__ __forceinline__ uint32_t pending_mask(uint32_t w) {
 #ifndef CF_MERGE_V
 #define CF_MERGE_V 4
 #endif
-static __global__ void __launch_bounds__(kBlock)
+// Minimum resident blocks per SM of merge / out (latency-bound gathers):
+// 6 (40 registers) ran them in 8.3 ms per step against 8.6 at 4 and 9.1 at
+// the compiler's own choice.
+#ifndef CF_MERGE_MINB
+#define CF_MERGE_MINB 6
+#endif
+static __global__ void __launch_bounds__(kBlock, CF_MERGE_MINB)
 k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
               const uint8_t* __restrict__ f2, uint64_t n) {
   constexpr int V = CF_MERGE_V;
@@ -677,7 +688,7 @@ k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
 // out: flags[j] = f1[dst[j]], V groups of four keys per thread and iteration
 // (byte stores when the caller's flags are not 4-byte aligned).
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(kBlock)
+static __global__ void __launch_bounds__(kBlock, CF_MERGE_MINB)
 k_slice_out(const uint32_t* __restrict__ dst, const uint8_t* __restrict__ f1,
             uint8_t* __restrict__ out, uint64_t n) {
   constexpr int V = CF_MERGE_V;
