@@ -338,12 +338,15 @@ cf_status ensure_slice(cf_filter* f, uint64_t n) {
 
 cf_status run_sliced(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
                      uint8_t* flags, cudaStream_t s) {
-  const uint64_t chunk = slice_chunk(f);
-  const uint64_t first = n < chunk ? n : chunk;
-  cf_status st = ensure_slice(f, first);
+  // Equal passes of at most the chunk: a short last pass would sweep the
+  // table's slices for few records.
+  const uint64_t cap = slice_chunk(f);
+  const uint64_t passes = (n + cap - 1) / cap;
+  const uint64_t chunk = (n + passes - 1) / passes;
+  cf_status st = ensure_slice(f, chunk);
   if (st != CF_OK) return st;
   if (op == OP_INSERT) {
-    st = ensure_queue(f, first, kSliceChunkMax);
+    st = ensure_queue(f, chunk, kSliceChunkMax);
     if (st != CF_OK) return st;
   }
   for (uint64_t off = 0; off < n; off += chunk) {
