@@ -28,9 +28,10 @@
 //   scan     exclusive prefix of the counts -> scatter cursors
 //   scatter  keys -> rec1 (the 64-bit hash of each key, grouped by slice),
 //            dst[j] = rec1 position of key j
-//   probe1   rec1 in order: the operation on bucket i1; pending records ->
-//            rec2 (grouped by i2's slice, cap2 records per slice, overflow in
-//            a spill region after the slices), link[p] = rec2 position
+//   probe1   rec1 in order (tiles staged in shared memory by TMA bulk
+//            copies): the operation on bucket i1; pending records -> rec2
+//            (grouped by i2's slice, cap2 records per slice, overflow in a
+//            spill region after the slices), link[p] = rec2 position
 //   probe2   rec2 in order: the operation on bucket i2; an insert whose two
 //            buckets are full joins the eviction queue (by rec2 position)
 //   evict    (insert) the eviction loop on the queued rec2 records
@@ -326,7 +327,7 @@ __device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
 // on the previous tile.  Records left pending are stashed in shared memory,
 // sorted by the slice of i2 once per tile, and written to rec2 as one run
 // per occupied slice (one claim on fill2 per run).
-// Shared memory: 20*T bytes + 4*S counters (T = kBlock*K <= 2048).
+// Shared memory: 20*T bytes + 4*S counters (T = kBlock*8 = 2048 records).
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
