@@ -221,7 +221,7 @@ def slice_kernel_bytes(phases: dict, W, chunk: int) -> dict:
         passes = sum(math.ceil(x / chunk) for x in sizes)
         sweep = tb * (1 if op == "query" else 2) * passes
         pf = max(0.0, pend[op])
-        out["slice_split"] += n * (8 + 8 + 8 + 4)
+        out["slice_split"] += n * (8 + 8 + 4)  # key read, rec1 write, dst write
         out["slice_probe1"] += n * (8 + 1 + pf * (8 + 4)) + sweep
         out["slice_probe2"] += n * pf * (8 + 1) + sweep
         out["slice_merge"] += n * (2 + pf * (4 + 1) + 4 + 1 + 1)
@@ -369,8 +369,8 @@ def gpu_arm(args):
                                    ("query", med["query"], W.n_queries),
                                    ("delete", med["delete"], W.n_deletes))},
         # Kernels launched in the timed steps, from the per-kernel timer (one
-        # timer record covers hist + scan + scatter, and merge + out).
-        "gpu_launches": sum(n_l * {"slice_split": 3, "slice_merge": 2}.get(k, 1)
+        # timer record covers merge + out).
+        "gpu_launches": sum(n_l * {"slice_merge": 2}.get(k, 1)
                             for k, (n_l, _) in ktimes.items()),
         "checks": {"insert_ok": ins_ok, "insert_fail": W.n_insert - ins_ok,
                    "query_pos_found": q_pos, "query_pos": W.n_queries // 2,

@@ -190,7 +190,7 @@ cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk);
  *    larger slices.  CF_EINVAL if smaller than one bucket.
  *  - max_chunk: keys per sliced pass (0: 2^28, at most 2^30, CF_EINVAL
  *    above).  Larger batches run as consecutive passes.
- *  - Scratch: about 36 bytes per key of a pass (its largest pass so far),
+ *  - Scratch: about 48 bytes per key of a pass (its largest pass so far),
  *    allocated by the library on the first sliced call and freed by
  *    cf_destroy or by a change of slice_bytes / max_chunk.  CF_ENOMEM if it
  *    cannot be allocated.

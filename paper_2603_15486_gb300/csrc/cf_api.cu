@@ -4,7 +4,7 @@
 //   [control block 256 B][victim log, 16 B per entry][table]
 // (each piece 256-byte aligned), plus library-owned scratch: the eviction
 // work queue of the insert (4 bytes per key of the largest chunk seen), the
-// scratch of the slice-partitioned path (about 36 bytes per key of its chunk)
+// scratch of the slice-partitioned path (about 48 bytes per key of its chunk)
 // and, for the *_host calls, two staging slots of keys and flags.
 #include <cuda_runtime.h>
 
@@ -291,8 +291,11 @@ void free_slice(cf_filter* f) {
 }
 
 // Scratch for chunks of up to n keys (one allocation, 256-byte aligned
-// pieces).  rec2 holds S regions of cap2 records plus a spill region of n:
-// cap2 = n/S + 6 sqrt(n/S) + 64 keeps uniform hashes inside their slice.
+// pieces).  rec1 and rec2 hold S regions plus a spill region of n:
+// n/S + 6 sqrt(n/S) + 64 records per region keep uniform hashes inside their
+// slice (rec1's rounded up to 256 records, so that its regions and tiles
+// start on 2 KB boundaries).  Positions in rec1 and rec2 fit 32 bits: both
+// hold at most about 2n + S * (6 sqrt(n/S) + 320) records, n <= 2^30.
 cf_status ensure_slice(cf_filter* f, uint64_t n) {
   uint32_t shift = 0, S = 0;
   slice_geometry(f, &shift, &S);
@@ -301,6 +304,8 @@ cf_status ensure_slice(cf_filter* f, uint64_t n) {
   free_slice(f);
   const double per = double(n) / S;
   const uint64_t cap2 = uint64_t(per + 6.0 * sqrt(per)) + 64;
+  const uint64_t cap1 = (cap2 + 255) / 256 * 256;
+  const uint64_t n1 = uint64_t(S) * cap1 + n;
   const uint64_t n2 = uint64_t(S) * cap2 + n;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -308,11 +313,12 @@ cf_status ensure_slice(cf_filter* f, uint64_t n) {
     off += align256(bytes);
     return o;
   };
-  // Counters one per 128-byte line (32 words apart).
-  const size_t o_cursor = take(size_t(S) * 128);
+  // Counters one per 128-byte line (32 words apart); fill1 and fill2 are
+  // adjacent so that one memset clears both.
+  const size_t o_fill1 = take(size_t(S + 1) * 128);
   const size_t o_fill2 = take(size_t(S + cfk::kFill2Extra) * 128);
-  const size_t o_dst = take(n * 4), o_rec1 = take(n * 8), o_f1 = take(n);
-  const size_t o_link = take(n * 4), o_rec2 = take(n2 * 8), o_f2 = take(n2);
+  const size_t o_dst = take(n * 4), o_rec1 = take(n1 * 8), o_f1 = take(n1);
+  const size_t o_link = take(n1 * 4), o_rec2 = take(n2 * 8), o_f2 = take(n2);
   char* mem = nullptr;
   if (cudaMalloc(&mem, off) != cudaSuccess) {
     cudaGetLastError();
@@ -322,8 +328,9 @@ cf_status ensure_slice(cf_filter* f, uint64_t n) {
   cfk::SliceBufs& b = f->sb;
   b.n_slices = S;
   b.shift = shift;
+  b.cap1 = cap1;
   b.cap2 = cap2;
-  b.cursor = reinterpret_cast<uint32_t*>(mem + o_cursor);
+  b.fill1 = reinterpret_cast<uint32_t*>(mem + o_fill1);
   b.fill2 = reinterpret_cast<uint32_t*>(mem + o_fill2);
   b.dst = reinterpret_cast<uint32_t*>(mem + o_dst);
   b.rec1 = reinterpret_cast<uint64_t*>(mem + o_rec1);

@@ -24,21 +24,24 @@
 // leave open anyway.
 //
 // Passes over a chunk of n keys, S slices:
-//   hist     keys -> per-slice counts of i1's slice
-//   scan     exclusive prefix of the counts -> scatter cursors
-//   scatter  keys -> rec1 (the 64-bit hash of each key, grouped by slice),
-//            dst[j] = rec1 position of key j
-//   probe1   rec1 in order (tiles staged in shared memory by TMA bulk
-//            copies): the operation on bucket i1; pending records -> rec2
-//            (grouped by i2's slice, cap2 records per slice, overflow in a
-//            spill region after the slices), link[p] = rec2 position
-//   probe2   rec2 in order: the operation on bucket i2; an insert whose two
-//            buckets are full joins the eviction queue (by rec2 position)
+//   scatter  keys -> rec1 (the 64-bit hash of each key, grouped by i1's
+//            slice: cap1 records per slice, overflow in a spill region
+//            after the slices), dst[j] = rec1 position of key j
+//   probe1   rec1 regions in order (tiles staged in shared memory by TMA
+//            bulk copies): the operation on bucket i1; pending records ->
+//            rec2 (grouped by i2's slice the same way, cap2 records per
+//            slice and a spill region), link[p] = rec2 position
+//   probe2   rec2 regions in order: the operation on bucket i2; an insert
+//            whose two buckets are full joins the eviction queue (by rec2
+//            position)
 //   evict    (insert) the eviction loop on the queued rec2 records
 //   merge    f1[p] = f2[link[p]] wherever f1[p] is pending
 //   out      flags[j] = f1[dst[j]]
-// Without a flags array the passes that only carry results (dst, f1, link,
-// f2, merge, out) are skipped.
+// The region capacities (the expected count plus six standard deviations)
+// hold a batch of distinct uniform hashes, so no counting pass precedes the
+// scatter; repeated keys or skewed batches only move records to the spill
+// region.  Without a flags array the passes that only carry results (dst,
+// f1, link, f2, merge, out) are skipped.
 #pragma once
 
 #include "cf_kernels.cuh"
@@ -50,8 +53,10 @@ constexpr uint8_t kPending = 0xFF;
 // apart): every block tile bumps one counter per slice, and counters packed
 // into a few lines would serialise those atomics on a few L2 slices.
 constexpr uint32_t kCtrStride = 32;
-// fill2 holds S per-slice counters, then the spill count (index S) and the
-// dynamic tile counters of probe2 (S + 1) and probe1 (S + 2): kFill2Extra.
+// fill1 holds S per-slice counters and the spill count (index S); fill2
+// the same for rec2, then the dynamic tile counters of probe2 (S + 1) and
+// probe1 (S + 2): kFill2Extra.  The two arrays are zeroed together before
+// the scatter.
 
 enum : int { SOP_INSERT = 0, SOP_CONTAINS = 1, SOP_REMOVE = 2 };
 
@@ -69,9 +74,8 @@ enum : int { SOP_INSERT = 0, SOP_CONTAINS = 1, SOP_REMOVE = 2 };
 #ifndef CF_SLICE2_MINB
 #define CF_SLICE2_MINB CF_SLICE_MINB
 #endif
-// Minimum resident blocks per SM of the split kernels (hist, scatter): 4
-// (64 registers) ran the split in 17.4 ms per step against 18.1 at the
-// compiler's own choice.
+// Minimum resident blocks per SM of the scatter: 4 (64 registers) ran the
+// split in 17.4 ms per step against 18.1 at the compiler's own choice.
 #ifndef CF_SPLIT_MINB
 #define CF_SPLIT_MINB 4
 #endif
@@ -127,76 +131,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 constexpr uint32_t kErrAsyncCopy = 4u;  // error_word bit: a bulk copy never completed
 
-// ---------------------------------------------------------------------------
-// hist: counts of i1's slice.  Each block bins its keys in shared memory and
-// adds its bins to the global histogram once.
-// ---------------------------------------------------------------------------
-template <class G, int U>
-__global__ void __launch_bounds__(kBlock, CF_SPLIT_MINB)
-k_slice_hist(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
-             uint32_t shift, uint32_t S, uint32_t* __restrict__ hist) {
-  extern __shared__ uint32_t s_cnt[];
-  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
-  __syncthreads();
-  const uint64_t tile = uint64_t(blockDim.x) * U;
-  for (uint64_t t0 = blockIdx.x * tile; t0 < n; t0 += uint64_t(gridDim.x) * tile) {
-    uint64_t v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
-      v[u] = i < n ? ld_stream_u64(keys + i) : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
-      if (i < n) atomicAdd(&s_cnt[hash_primary<G>(d, v[u]).i1 >> shift], 1u);
-    }
-  }
-  __syncthreads();
-  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x)
-    if (s_cnt[s]) atomicAdd(&hist[s * kCtrStride], s_cnt[s]);
-}
-
-// ---------------------------------------------------------------------------
-// scan: exclusive prefix of the S counts in place (one block of 1024), and
-// the rec2 fill counters and tile counters zeroed.
-// ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(1024)
-k_slice_scan(uint32_t* __restrict__ cursor, uint32_t S, uint32_t* __restrict__ fill2) {
-  __shared__ uint32_t warp_sum[32];
-  __shared__ uint32_t carry;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint32_t base = 0; base < S; base += blockDim.x) {
-    const uint32_t s = base + threadIdx.x;
-    const uint32_t v = s < S ? cursor[s * kCtrStride] : 0u;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= uint32_t(o)) x += y;
-    }
-    if (lane == 31) warp_sum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t t = warp_sum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
-        if (lane >= uint32_t(o)) t += y;
-      }
-      warp_sum[lane] = t;
-    }
-    __syncthreads();
-    if (s < S) cursor[s * kCtrStride] = carry + (warp ? warp_sum[warp - 1] : 0u) + x - v;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += warp_sum[31];
-    __syncthreads();
-  }
-  for (uint32_t s = threadIdx.x; s < S + kFill2Extra; s += blockDim.x) fill2[s * kCtrStride] = 0;
-}
-
 // Exclusive prefix of in[0..S) into out[0..S) by the whole block (each
 // thread sums a run of consecutive bins, one warp scans the run sums).
 // Ends with a barrier; tmp is 32 words of shared memory.
@@ -242,28 +176,77 @@ __device__ __forceinline__ uint32_t slice_of_h(const DevFilter& d, uint64_t h,
   return hash_from_h<G>(d, h).i1 >> shift;
 }
 
+// Position of the rk-th record of slice s in a block tile's run, from the
+// tile's claim (base = fill[s] before the claim, cnt records): the first
+// cap - base go to the slice's region, the rest to the spill region after
+// the S regions.
+__device__ __forceinline__ uint64_t region_pos(uint32_t s, uint32_t rk,
+                                               uint32_t base, uint32_t cnt,
+                                               uint32_t spill, uint64_t cap,
+                                               uint32_t S) {
+  const uint64_t room = base >= cap ? 0 : cap - base;
+  const uint32_t in = room < cnt ? uint32_t(room) : cnt;
+  return rk < in ? uint64_t(s) * cap + base + rk
+                 : uint64_t(S) * cap + spill + (rk - in);
+}
+
+// A block tile's claims: for every slice with s_cnt[s] records, s_base[s] =
+// fill[s] before adding them, and s_spill[s] = the spill count before
+// adding the part that does not fit the region (fill[S] counts the spill).
+// *spilled becomes nonzero if any run of the tile reaches the spill region;
+// while it stays zero, the rk-th record of slice s goes to s*cap + s_base[s]
+// + rk (all positions fit 32 bits).
+__device__ __forceinline__ void claim_runs(const uint32_t* s_cnt, uint32_t* s_base,
+                                           uint32_t* s_spill, uint32_t S,
+                                           uint32_t* fill, uint64_t cap,
+                                           uint32_t* spilled) {
+  for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
+    const uint32_t cnt = s_cnt[s];
+    if (!cnt) continue;
+    const uint32_t base = atomicAdd(&fill[s * kCtrStride], cnt);
+    const uint64_t room = base >= cap ? 0 : cap - base;
+    s_base[s] = base;
+    s_spill[s] = 0;
+    if (room < cnt) {
+      s_spill[s] = atomicAdd(&fill[S * kCtrStride], cnt - uint32_t(room));
+      *spilled = 1;
+    }
+  }
+}
+
+// Records in region r of a split (S slice regions of cap, then the spill).
+__device__ __forceinline__ uint32_t region_len(const uint32_t* fill, uint32_t r,
+                                               uint32_t S, uint64_t cap) {
+  const uint32_t f = __ldcg(fill + r * kCtrStride);
+  return r < S && f > cap ? uint32_t(cap) : f;
+}
+
 // ---------------------------------------------------------------------------
 // scatter (a multi-split): each block tile of kBlock*U keys is binned by
 // slice in shared memory (a rank per key), sorted by slice inside shared
 // memory, and written out as one contiguous run per occupied slice (one
-// global cursor bump per run), so consecutive threads store consecutive
+// claim on fill1 per run), so consecutive threads store consecutive
 // records.  dst[] is written in key order.
-// Shared memory: 3*S counters + 8*kBlock*U bytes.
+// Shared memory: 4*S counters + 8*kBlock*U bytes.
 // ---------------------------------------------------------------------------
 template <class G, int U>
 __global__ void __launch_bounds__(kBlock, CF_SPLIT_MINB)
 k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
-                uint32_t shift, uint32_t S, uint32_t* __restrict__ cursor,
-                uint64_t* __restrict__ rec1, uint32_t* __restrict__ dst) {
+                SliceBufs sb, uint32_t* __restrict__ dst) {
   extern __shared__ uint64_t sm64[];
   constexpr uint32_t T = kBlock * U;
+  const uint32_t S = sb.n_slices, shift = sb.shift;
   uint64_t* stash = sm64;                                   // [T]
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(sm64 + T);  // [S]
   uint32_t* s_off = s_cnt + S;                              // [S]
   uint32_t* s_base = s_off + S;                             // [S]
+  uint32_t* s_spill = s_base + S;                           // [S]
   __shared__ uint32_t tmp[32];
+  __shared__ uint32_t s_spilled;
+  const uint32_t cap = uint32_t(sb.cap1);
   for (uint64_t t0 = blockIdx.x * uint64_t(T); t0 < n; t0 += uint64_t(gridDim.x) * T) {
     for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
+    if (threadIdx.x == 0) s_spilled = 0;
     __syncthreads();
     uint64_t h[U];
     uint32_t slrk[U];  // slice << 16 | rank
@@ -284,16 +267,21 @@ k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
     }
     __syncthreads();
     block_scan_excl(s_cnt, s_off, S, tmp);
-    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x)
-      if (s_cnt[s]) s_base[s] = atomicAdd(&cursor[s * kCtrStride], s_cnt[s]);
+    claim_runs(s_cnt, s_base, s_spill, S, sb.fill1, sb.cap1, &s_spilled);
     __syncthreads();
+    const bool spilled = s_spilled != 0;
+    auto pos = [&](uint32_t sl, uint32_t rk) -> uint32_t {
+      return spilled ? uint32_t(region_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl],
+                                           sb.cap1, S))
+                     : sl * cap + s_base[sl] + rk;
+    };
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint64_t i = t0 + uint64_t(u) * blockDim.x + threadIdx.x;
       if (i < n) {
         const uint32_t sl = slrk[u] >> 16, rk = slrk[u] & 0xFFFFu;
         stash[s_off[sl] + rk] = h[u];
-        if (dst) st_cs_u32(dst + i, s_base[sl] + rk);
+        if (dst) st_cs_u32(dst + i, pos(sl, rk));
       }
     }
     __syncthreads();
@@ -301,40 +289,29 @@ k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
     for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
       const uint64_t hv = stash[j];
       const uint32_t sl = slice_of_h<G>(d, hv, shift);
-      rec1[s_base[sl] + (j - s_off[sl])] = hv;
+      sb.rec1[pos(sl, j - s_off[sl])] = hv;
     }
     __syncthreads();
   }
 }
 
-// rec2 position of the rk-th pending record of slice s in a block tile,
-// from the tile's claim (base = fill2[s] before the claim, cnt records):
-// the first cap2 - base go to the slice, the rest to the spill region.
-__device__ __forceinline__ uint64_t rec2_pos(uint32_t s, uint32_t rk,
-                                             uint32_t base, uint32_t cnt,
-                                             uint32_t spill, uint64_t cap2,
-                                             uint32_t S) {
-  const uint64_t room = base >= cap2 ? 0 : cap2 - base;
-  const uint32_t in = room < cnt ? uint32_t(room) : cnt;
-  return rk < in ? uint64_t(s) * cap2 + base + rk
-                 : uint64_t(S) * cap2 + spill + (rk - in);
-}
-
 // ---------------------------------------------------------------------------
-// probe1: the operation on bucket i1 for rec1 records in order.  A block
-// tile is kBlock*8 records (thread t takes records t, t + kBlock, ...),
-// staged in shared memory by a TMA bulk copy issued while the block works
-// on the previous tile.  Records left pending are stashed in shared memory,
-// sorted by the slice of i2 once per tile, and written to rec2 as one run
-// per occupied slice (one claim on fill2 per run).
-// Shared memory: 20*T bytes + 4*S counters (T = kBlock*8 = 2048 records).
+// probe1: the operation on bucket i1 for rec1 records, regions in order.  A
+// block tile is up to kBlock*8 records of one region (thread t takes
+// records t, t + kBlock, ...), staged in shared memory by a TMA bulk copy
+// issued while the block works on the previous tile.  Records left pending
+// are stashed in shared memory, sorted by the slice of i2 once per tile,
+// and written to rec2 as one run per occupied slice (one claim on fill2 per
+// run).
+// Shared memory: 20*T bytes + 4*S counters + 4*(S + 2) tile starts +
+// 4*(S + 1) region lengths (T = kBlock*8 = 2048 records).
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 template <class G, int OP, int K>
 __global__ void __launch_bounds__(kBlock, CF_SLICE_MINB)
-k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
+k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
   // R rounds of K records per thread: every tile holds 8 records per thread
   // whatever the bucket size (K = 8 / 4 / 2 / 1 for 8 / 16 / 32 / 64-byte
   // buckets), so the per-tile work (barriers, prefix, claims) stays amortised.
@@ -345,38 +322,62 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
   static_assert(T <= 2048, "shared entries pack an 11-bit tile index");
   extern __shared__ uint64_t sm64[];
   const uint32_t S = sb.n_slices;
+  const uint32_t NR = S + 1;  // rec1 regions: S slices, then the spill
   uint64_t* pref = sm64;                                            // [T] next tile's records
   uint64_t* stash_h = sm64 + T;                                     // [T] by tile index
   uint32_t* s_order = reinterpret_cast<uint32_t*>(sm64 + 2 * T);   // [T] index | slice << 11
-  uint32_t* s_cnt = s_order + T;                                    // [S]
-  uint32_t* s_off = s_cnt + S;                                      // [S]
+  uint32_t* s_cnt = s_order + T;                                    // [S + 1]
+  uint32_t* s_off = s_cnt + NR;                                     // [S]
   uint32_t* s_base = s_off + S;                                     // [S]
   uint32_t* s_spill = s_base + S;                                   // [S]
+  uint32_t* s_tstart = s_spill + S;                                 // [S + 2]
+  uint32_t* s_len = s_tstart + NR + 1;                              // [S + 1]
   __shared__ uint32_t tmp[32];
-  __shared__ uint32_t s_next;
+  __shared__ uint32_t s_next_p, s_next_cnt, s_spilled;
   __shared__ __align__(8) uint64_t s_bar;
   TileCounts c;
+  // Records and first tile of every region (tiles never straddle two
+  // regions), and the number of tiles after the last one.
+  for (uint32_t r = threadIdx.x; r < NR; r += blockDim.x) {
+    s_len[r] = region_len(sb.fill1, r, S, sb.cap1);
+    s_cnt[r] = (s_len[r] + T - 1) / T;
+  }
+  __syncthreads();
+  block_scan_excl(s_cnt, s_tstart, NR, tmp);
+  if (threadIdx.x == 0) s_tstart[NR] = s_tstart[NR - 1] + s_cnt[NR - 1];
   // Tiles are handed out in order by a counter, so the blocks at work stay
   // within a window of consecutive tiles (one or two slices) instead of
   // drifting apart as a static grid stride lets them.  One thread copies the
   // next tile's records into shared memory (TMA bulk copy) while the block
-  // works on the current one.
+  // works on the current one; a tile of cnt records copies cnt & ~1 of
+  // them (16-byte multiples; region starts are multiples of 256 records)
+  // and the block loads an odd last one itself.
   uint32_t* tile_ctr = sb.fill2 + (S + 2) * kCtrStride;
-  auto tile_bytes = [&](uint32_t tile) -> uint32_t {
-    const uint32_t t0 = tile * T;
-    return t0 >= n ? 0u : ((n - t0 < T ? n - t0 : T) * 8u) & ~15u;
+  uint32_t reg = 0;  // thread 0: region of the block's latest tile (its tiles only grow)
+  auto fetch = [&]() {  // thread 0
+    const uint32_t t = atomicAdd(tile_ctr, 1u);
+    if (t >= s_tstart[NR]) {
+      s_next_cnt = 0;
+      return;
+    }
+    while (s_tstart[reg + 1] <= t) ++reg;  // stops at a nonempty region: t < tiles
+    const uint32_t k0 = (t - s_tstart[reg]) * T;
+    const uint32_t len = s_len[reg];
+    const uint32_t cnt = len - k0 < T ? len - k0 : T;
+    const uint32_t p = reg * uint32_t(sb.cap1) + k0;
+    s_next_p = p;
+    s_next_cnt = cnt;
+    bulk_load(&s_bar, pref, sb.rec1 + p, (cnt & ~1u) * 8u);
   };
+  __syncthreads();  // tile starts in place
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
-    s_next = atomicAdd(tile_ctr, 1u);
-    if (s_next * T < n) bulk_load(&s_bar, pref, sb.rec1 + size_t(s_next) * T, tile_bytes(s_next));
+    fetch();
   }
   __syncthreads();
-  uint32_t tile = s_next;
+  uint32_t t0 = s_next_p, tcnt = s_next_cnt;
   uint32_t parity = 0;
-  for (;;) {
-    const uint32_t t0 = tile * T;
-    if (t0 >= n) break;
+  while (tcnt) {
     if (!mbar_wait(&s_bar, parity)) {
       // The copy did not complete: report it and leave this tile (its
       // records stay unprocessed; the error bit tells the caller).
@@ -386,23 +387,21 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
     }
     parity ^= 1u;
     // Record i of this thread: tile index loc(i) = i*kBlock + thread (lane-
-    // strided: conflict-free reads of the staged tile, coalesced stores).
-    const uint32_t copied = tile_bytes(tile) / 8u;  // records now in pref
+    // strided: conflict-free reads of the staged tile, coalesced stores),
+    // at rec1 position t0 + loc.
+    const uint32_t copied = tcnt & ~1u;  // records now in pref
     uint64_t hr[N];
     bool vr[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
-      vr[i] = t0 + loc < n;
+      vr[i] = loc < tcnt;
       hr[i] = loc < copied ? pref[loc] : (vr[i] ? ld_stream_u64(sb.rec1 + t0 + loc) : 0ull);
     }
     for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
+    if (threadIdx.x == 32) s_spilled = 0;
     __syncthreads();  // pref consumed, counters zeroed
-    if (threadIdx.x == 0) {
-      s_next = atomicAdd(tile_ctr, 1u);
-      if (s_next * T < n)
-        bulk_load(&s_bar, pref, sb.rec1 + size_t(s_next) * T, tile_bytes(s_next));
-    }
+    if (threadIdx.x == 0) fetch();
     uint32_t slrk[N];  // slice << 16 | rank of a pending record, else kNoSlot
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -453,17 +452,16 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
     }
     __syncthreads();
     block_scan_excl(s_cnt, s_off, S, tmp);
-    for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) {
-      const uint32_t cnt = s_cnt[s];
-      if (!cnt) continue;
-      const uint32_t base = atomicAdd(&sb.fill2[s * kCtrStride], cnt);
-      const uint64_t room = base >= sb.cap2 ? 0 : sb.cap2 - base;
-      s_base[s] = base;
-      s_spill[s] = room < cnt ? atomicAdd(&sb.fill2[S * kCtrStride], cnt - uint32_t(room))
-                              : 0u;
-    }
+    claim_runs(s_cnt, s_base, s_spill, S, sb.fill2, sb.cap2, &s_spilled);
     const uint32_t np = s_off[S - 1] + s_cnt[S - 1];
     __syncthreads();
+    const bool spilled = s_spilled != 0;
+    const uint32_t cap2 = uint32_t(sb.cap2);
+    auto pos = [&](uint32_t sl, uint32_t rk) -> uint32_t {
+      return spilled ? uint32_t(region_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl],
+                                           sb.cap2, S))
+                     : sl * cap2 + s_base[sl] + rk;
+    };
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
@@ -471,7 +469,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
       if (slrk[i] != kNoSlot) {
         const uint32_t sl = slrk[i] >> 16, rk = slrk[i] & 0xFFFFu;
         s_order[s_off[sl] + rk] = loc | (sl << 11);
-        lk = uint32_t(rec2_pos(sl, rk, s_base[sl], s_cnt[sl], s_spill[sl], sb.cap2, S));
+        lk = pos(sl, rk);
       }
       if (want_flags && vr[i]) sb.link[t0 + loc] = lk;
     }
@@ -479,12 +477,11 @@ k_slice_probe1(DevFilter d, SliceBufs sb, uint32_t n, int want_flags) {
     for (uint32_t j = threadIdx.x; j < np; j += blockDim.x) {
       const uint32_t e = s_order[j];
       const uint32_t sl = e >> 11;
-      const uint64_t q = rec2_pos(sl, j - s_off[sl], s_base[sl], s_cnt[sl], s_spill[sl],
-                                  sb.cap2, S);
-      sb.rec2[q] = stash_h[e & 0x7FFu];
+      sb.rec2[pos(sl, j - s_off[sl])] = stash_h[e & 0x7FFu];
     }
     __syncthreads();
-    tile = s_next;
+    t0 = s_next_p;
+    tcnt = s_next_cnt;
   }
   if constexpr (OP == SOP_INSERT) {
     block_add(&d.ctrl->occupancy, c.ok);
@@ -628,8 +625,8 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
 
 // ---------------------------------------------------------------------------
 // merge: f1[p] = f2[link[p]] for pending records.  A thread takes V groups of
-// four records per iteration (V grid strides apart), so that up to 4*V of
-// its gathers are in flight together.
+// four rec1 positions per iteration (V grid strides apart), so that up to
+// 4*V of its gathers are in flight together.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t pending_mask(uint32_t w) {
   uint32_t m = 0;
@@ -649,26 +646,50 @@ __device__ __forceinline__ uint32_t pending_mask(uint32_t w) {
 #define CF_MERGE_MINB 6
 #endif
 static __global__ void __launch_bounds__(kBlock, CF_MERGE_MINB)
-k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
-              const uint8_t* __restrict__ f2, uint64_t n) {
+k_slice_merge(SliceBufs sb) {
   constexpr int V = CF_MERGE_V;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  const uint64_t n4 = n / 4;
-  uint32_t* f1w = reinterpret_cast<uint32_t*>(f1);
-  const uint4* link4 = reinterpret_cast<const uint4*>(link);
-  for (uint64_t v0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v0 < n4;
-       v0 += stride * V) {
-    uint32_t w[V], pend[V];
+  // Groups of four rec1 positions (cap1 is a multiple of four, so a group
+  // never straddles two regions): the records of every region, its number
+  // of groups and its first group in the order the threads walk them.
+  extern __shared__ uint32_t s_reg[];
+  __shared__ uint32_t tmp[32];
+  const uint32_t S = sb.n_slices, NR = S + 1;
+  uint32_t* s_len = s_reg;            // [S + 1]
+  uint32_t* s_gcnt = s_len + NR;      // [S + 1]
+  uint32_t* s_gstart = s_gcnt + NR;   // [S + 2]
+  for (uint32_t r = threadIdx.x; r < NR; r += blockDim.x) {
+    s_len[r] = region_len(sb.fill1, r, S, sb.cap1);
+    s_gcnt[r] = (s_len[r] + 3) / 4;
+  }
+  __syncthreads();
+  block_scan_excl(s_gcnt, s_gstart, NR, tmp);
+  if (threadIdx.x == 0) s_gstart[NR] = s_gstart[NR - 1] + s_gcnt[NR - 1];
+  __syncthreads();
+  const uint32_t total = s_gstart[NR];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t* f1w = reinterpret_cast<uint32_t*>(sb.f1);
+  const uint4* link4 = reinterpret_cast<const uint4*>(sb.link);
+  uint32_t r = 0;  // region of the thread's latest group (its groups only grow)
+  for (uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < total; g0 += stride * V) {
+    uint32_t w[V], pend[V], q[V];
     uint4 l[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-      const uint64_t v = v0 + u * stride;
-      w[u] = v < n4 ? ld_cs_u32(f1w + v) : 0u;
-      pend[u] = v < n4 ? pending_mask(w[u]) : 0u;
+      const uint32_t g = g0 + u * stride;
+      pend[u] = 0;
+      q[u] = 0;
+      if (g < total) {
+        while (s_gstart[r + 1] <= g) ++r;
+        const uint32_t off = (g - s_gstart[r]) * 4;
+        const uint32_t vc = s_len[r] - off;  // >= 1
+        q[u] = uint32_t((uint64_t(r) * sb.cap1 + off) / 4);
+        w[u] = ld_cs_u32(f1w + q[u]);
+        pend[u] = pending_mask(w[u]) & (vc >= 4 ? 0xFu : (1u << vc) - 1);
+      }
     }
 #pragma unroll
     for (int u = 0; u < V; ++u)
-      if (pend[u]) l[u] = link4[v0 + u * stride];
+      if (pend[u]) l[u] = link4[q[u]];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       if (!pend[u]) continue;
@@ -676,13 +697,10 @@ k_slice_merge(uint8_t* __restrict__ f1, const uint32_t* __restrict__ link,
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (pend[u] & (1u << j))
-          w[u] = (w[u] & ~(0xFFu << (8 * j))) | (uint32_t(f2[ls[j]]) << (8 * j));
-      f1w[v0 + u * stride] = w[u];
+          w[u] = (w[u] & ~(0xFFu << (8 * j))) | (uint32_t(sb.f2[ls[j]]) << (8 * j));
+      f1w[q[u]] = w[u];
     }
   }
-  for (uint64_t p = n4 * 4 + blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; p < n;
-       p += stride)
-    if (f1[p] == kPending) f1[p] = f2[link[p]];
 }
 
 // ---------------------------------------------------------------------------
@@ -726,6 +744,13 @@ k_slice_out(const uint32_t* __restrict__ dst, const uint8_t* __restrict__ f1,
 // ---------------------------------------------------------------------------
 // Launch sequence of one chunk.
 // ---------------------------------------------------------------------------
+// Dynamic shared memory near or above the 48 KB default (static shared
+// memory counts against it too) needs the kernel's opt-in.
+inline cudaError_t smem_opt_in(const void* fn, size_t bytes) {
+  if (bytes <= 40 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
 template <class G>
 struct SliceLaunch {
   static constexpr int KQ = Tiles<G, false>::K;
@@ -740,17 +765,14 @@ struct SliceLaunch {
                             int want, uint32_t* queue, cudaStream_t s,
                             KernelTimer* t) {
     constexpr uint32_t T = kBlock * 8;
-    const size_t smem = size_t(20) * T + size_t(16) * sb.n_slices;
+    const size_t smem = size_t(20) * T + size_t(24) * sb.n_slices + 16;
     auto p1 = k_slice_probe1<G, OP, K>;
-    if (smem > 48 * 1024) {
-      const cudaError_t ea =
-          cudaFuncSetAttribute(p1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (ea != cudaSuccess) return ea;
-    }
+    cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(p1), smem);
+    if (e != cudaSuccess) return e;
     if (t) t->begin(KK_SLICE_PROBE1, s);
-    p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, uint32_t(n), want);
+    p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, want);
     if (t) t->end(KK_SLICE_PROBE1, s);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto p2 = k_slice_probe2<G, OP, K>;
     const size_t smem2 = size_t(2) * (sb.n_slices + 1) * sizeof(uint32_t);
@@ -766,17 +788,17 @@ struct SliceLaunch {
     const int want = flags != nullptr;
     const uint32_t S = sb.n_slices;
     if (t) t->begin(KK_SLICE_SPLIT, s);
-    cudaError_t e =
-        cudaMemsetAsync(sb.cursor, 0, size_t(S) * kCtrStride * sizeof(uint32_t), s);
+    // fill1 and fill2 (and the tile counters after it) share one range.
+    const size_t ctr_bytes = reinterpret_cast<const char*>(sb.fill2 + (S + kFill2Extra) * kCtrStride) -
+                             reinterpret_cast<const char*>(sb.fill1);
+    cudaError_t e = cudaMemsetAsync(sb.fill1, 0, ctr_bytes, s);
     if (e != cudaSuccess) return e;
-    auto fh = k_slice_hist<G, U>;
-    fh<<<persistent_grid(fh, n, kBlock * U), kBlock, S * sizeof(uint32_t), s>>>(
-        d, keys, n, sb.shift, S, sb.cursor);
-    k_slice_scan<<<1, 1024, 0, s>>>(sb.cursor, S, sb.fill2);
     auto fs = k_slice_scatter<G, U>;
-    const size_t smem = size_t(8) * kBlock * U + size_t(12) * S;
-    fs<<<persistent_grid(fs, n, kBlock * U), kBlock, smem, s>>>(
-        d, keys, n, sb.shift, S, sb.cursor, sb.rec1, want ? sb.dst : nullptr);
+    const size_t smem = size_t(8) * kBlock * U + size_t(16) * S;
+    e = smem_opt_in(reinterpret_cast<const void*>(fs), smem);
+    if (e != cudaSuccess) return e;
+    fs<<<persistent_grid(fs, n, kBlock * U), kBlock, smem, s>>>(d, keys, n, sb,
+                                                                want ? sb.dst : nullptr);
     if (t) t->end(KK_SLICE_SPLIT, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -801,8 +823,8 @@ struct SliceLaunch {
     }
     if (!want) return cudaSuccess;
     if (t) t->begin(KK_SLICE_MERGE, s);
-    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 4 * CF_MERGE_V), kBlock, 0,
-                    s>>>(sb.f1, sb.link, sb.f2, n);
+    k_slice_merge<<<persistent_grid(k_slice_merge, n, kBlock * 4 * CF_MERGE_V), kBlock,
+                    size_t(12) * (S + 2), s>>>(sb);
     k_slice_out<<<persistent_grid(k_slice_out, n, kBlock * 4 * CF_MERGE_V), kBlock, 0, s>>>(
         sb.dst, sb.f1, flags, n);
     if (t) t->end(KK_SLICE_MERGE, s);

@@ -173,6 +173,28 @@ def test_sliced_spill_with_duplicates(cf):
     assert st["occupancy"] == int(np.count_nonzero(slots))
 
 
+@pytest.mark.parametrize("f,b", [(16, 4), (8, 8)])
+@pytest.mark.parametrize("chunk", [0, 9000])
+def test_sliced_first_split_spill(cf, f, b, chunk):
+    """One key repeated over most of a batch overflows its slice's region in
+    the first split (the expected share plus six standard deviations), so
+    most records take the spill region after the slices; with the chunk
+    limit the batch runs as passes whose spill starts empty each time.
+    Every result is still exact."""
+    m = 1 << 12
+    o, ks = _oracle_table(f, b, "xor", m, alpha=0.9, seed=11)
+    neg = workloads.keys(11, 4000, start=ks.size)
+    q = np.concatenate([ks[7:8].repeat(20000), ks[:4000], neg, neg[:3].repeat(700)])
+    np.random.default_rng(5).shuffle(q)
+    g = _sliced(cf.CuckooFilter(m, f, b, 500), chunk=chunk)
+    g.load(o.snapshot())
+    g.set_kernel_timing(True)
+    got = g.contains(to_dev(q)).cpu().numpy()
+    assert _ran_sliced(g)
+    assert np.array_equal(got, o.contains_batch(q))
+    assert g.stats()["error_word"] == 0
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 4099 * 3 + 7])
 def test_sliced_chunks_tails_and_alignment(cf, n):
     """Batches split into passes of at most 4099 keys, sizes that leave
