@@ -429,7 +429,7 @@ cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
  * launch (around each group of launches for the sliced passes).  Index 0:
  * insert phase 1 (direct insertion into i1 / i2), 1: insert phase 2
  * (eviction loop, both paths), 2: contains, 3: remove; slice-partitioned
- * path (cf_set_slicing): 4: grouping by slice (histogram, prefix, scatter),
+ * path (cf_set_slicing): 4: grouping by slice (counter reset, scatter),
  * 5: bucket-i1 pass, 6: bucket-i2 pass, 7: results back to key order.
  * cf_read_kernel_times waits for the recorded events, sums their elapsed
  * times and (reset != 0) recycles them. */

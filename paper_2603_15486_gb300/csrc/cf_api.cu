@@ -330,6 +330,7 @@ cf_status ensure_slice(cf_filter* f, uint64_t n) {
   b.shift = shift;
   b.cap1 = cap1;
   b.cap2 = cap2;
+  b.rec2_len = n2;
   b.fill1 = reinterpret_cast<uint32_t*>(mem + o_fill1);
   b.fill2 = reinterpret_cast<uint32_t*>(mem + o_fill2);
   b.dst = reinterpret_cast<uint32_t*>(mem + o_dst);

@@ -679,7 +679,7 @@ enum KernelKind : int {
   KK_INSERT_EVICT = 1,
   KK_CONTAINS = 2,
   KK_REMOVE = 3,
-  KK_SLICE_SPLIT = 4,   // slice-partitioned path: hist + scan + scatter
+  KK_SLICE_SPLIT = 4,   // slice-partitioned path: scatter
   KK_SLICE_PROBE1 = 5,  // ... bucket i1 pass
   KK_SLICE_PROBE2 = 6,  // ... bucket i2 pass
   KK_SLICE_MERGE = 7,   // ... merge + out (results back to key order)

@@ -30,12 +30,14 @@
 //   probe1   rec1 regions in order (tiles staged in shared memory by TMA
 //            bulk copies): the operation on bucket i1; pending records ->
 //            rec2 (grouped by i2's slice the same way, cap2 records per
-//            slice and a spill region), link[p] = rec2 position
+//            slice and a spill region); link[p] = the rec2 position of a
+//            pending record, else its flag (tagged kSettled)
 //   probe2   rec2 regions in order: the operation on bucket i2; an insert
 //            whose two buckets are full joins the eviction queue (by rec2
 //            position)
 //   evict    (insert) the eviction loop on the queued rec2 records
-//   merge    f1[p] = f2[link[p]] wherever f1[p] is pending
+//   merge    f1[p] = the flag in link[p], or f2 at the rec2 position it
+//            holds
 //   out      flags[j] = f1[dst[j]]
 // The region capacities (the expected count plus six standard deviations)
 // hold a batch of distinct uniform hashes, so no counting pass precedes the
@@ -48,7 +50,9 @@
 
 namespace cfk {
 
-constexpr uint8_t kPending = 0xFF;
+// link[p] of a rec1 record: its rec2 position while pending, else
+// kSettled | flag (every rec2 position lies below kSettled).
+constexpr uint32_t kSettled = 0xFFFFFF00u;
 // Per-slice counters are spread one per 128-byte line (kCtrStride words
 // apart): every block tile bumps one counter per slice, and counters packed
 // into a few lines would serialise those atomics on a few L2 slices.
@@ -307,8 +311,6 @@ k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
 // 4*(S + 1) region lengths (T = kBlock*8 = 2048 records).
 // ---------------------------------------------------------------------------
 
-constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
-
 template <class G, int OP, int K>
 __global__ void __launch_bounds__(kBlock, CF_SLICE_MINB)
 k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
@@ -402,7 +404,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
     if (threadIdx.x == 32) s_spilled = 0;
     __syncthreads();  // pref consumed, counters zeroed
     if (threadIdx.x == 0) fetch();
-    uint32_t slrk[N];  // slice << 16 | rank of a pending record, else kNoSlot
+    uint32_t slrk[N];  // slice << 16 | rank of a pending record, else kSettled | flag
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       bool valid[K];
@@ -430,24 +432,21 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
       for (int k = 0; k < K; ++k) {
         const int i = r * K + k;
         const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
-        slrk[i] = kNoSlot;
-        uint8_t v = 0;
+        slrk[i] = kSettled;  // settled with flag 0 (or not a record)
         if (valid[k] && res[k] == TI_FULL) {
           const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
           slrk[i] = (sl << 16) | atomicAdd(&s_cnt[sl], 1u);
           stash_h[loc] = hr[i];
-          v = kPending;
         } else if (valid[k]) {
           if (res[k] == TI_OK) {
-            v = 1;
+            slrk[i] = kSettled | 1u;
             c.ok++;
           } else {
-            v = 2;
+            slrk[i] = kSettled | 2u;
             c.cont++;
             if (OP == SOP_INSERT) log_victim(d, tag[k], bkt[k]);
           }
         }
-        if (want_flags && valid[k]) st_flag(sb.f1 + t0 + loc, v);
       }
     }
     __syncthreads();
@@ -465,9 +464,9 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
-      uint32_t lk = 0;
-      if (slrk[i] != kNoSlot) {
-        const uint32_t sl = slrk[i] >> 16, rk = slrk[i] & 0xFFFFu;
+      uint32_t lk = slrk[i];
+      if (lk < kSettled) {
+        const uint32_t sl = lk >> 16, rk = lk & 0xFFFFu;
         s_order[s_off[sl] + rk] = loc | (sl << 11);
         lk = pos(sl, rk);
       }
@@ -624,18 +623,13 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
 }
 
 // ---------------------------------------------------------------------------
-// merge: f1[p] = f2[link[p]] for pending records.  A thread takes V groups of
-// four rec1 positions per iteration (V grid strides apart), so that up to
-// 4*V of its gathers are in flight together.
+// merge: f1[p] = the flag of rec1 record p: link[p] when probe1 settled it,
+// else f2 at the rec2 position link[p] holds.  Records are walked in rec1
+// order, the order in which probe1 wrote rec2, so the f2 gathers stay
+// within a window that L2 holds.  A thread takes V groups of four rec1
+// positions per iteration (V grid strides apart), so that up to 4*V of its
+// gathers are in flight together.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t pending_mask(uint32_t w) {
-  uint32_t m = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (((w >> (8 * j)) & 0xFFu) == kPending) m |= 1u << j;
-  return m;
-}
-
 #ifndef CF_MERGE_V
 #define CF_MERGE_V 4
 #endif
@@ -669,36 +663,39 @@ k_slice_merge(SliceBufs sb) {
   const uint32_t stride = gridDim.x * blockDim.x;
   uint32_t* f1w = reinterpret_cast<uint32_t*>(sb.f1);
   const uint4* link4 = reinterpret_cast<const uint4*>(sb.link);
+  const uint32_t cap = uint32_t(sb.cap1);
   uint32_t r = 0;  // region of the thread's latest group (its groups only grow)
   for (uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < total; g0 += stride * V) {
-    uint32_t w[V], pend[V], q[V];
+    uint32_t q[V], vc[V];
     uint4 l[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
       const uint32_t g = g0 + u * stride;
-      pend[u] = 0;
-      q[u] = 0;
+      vc[u] = 0;
       if (g < total) {
         while (s_gstart[r + 1] <= g) ++r;
         const uint32_t off = (g - s_gstart[r]) * 4;
-        const uint32_t vc = s_len[r] - off;  // >= 1
-        q[u] = uint32_t((uint64_t(r) * sb.cap1 + off) / 4);
-        w[u] = ld_cs_u32(f1w + q[u]);
-        pend[u] = pending_mask(w[u]) & (vc >= 4 ? 0xFu : (1u << vc) - 1);
+        vc[u] = s_len[r] - off;  // records in the group: 1, 2, 3 or >= 4
+        q[u] = (r * cap + off) / 4;
+        l[u] = __ldcs(link4 + q[u]);
       }
     }
 #pragma unroll
-    for (int u = 0; u < V; ++u)
-      if (pend[u]) l[u] = link4[q[u]];
-#pragma unroll
     for (int u = 0; u < V; ++u) {
-      if (!pend[u]) continue;
+      if (!vc[u]) continue;
       const uint32_t ls[4] = {l[u].x, l[u].y, l[u].z, l[u].w};
+      uint32_t w = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (pend[u] & (1u << j))
-          w[u] = (w[u] & ~(0xFFu << (8 * j))) | (uint32_t(sb.f2[ls[j]]) << (8 * j));
-      f1w[q[u]] = w[u];
+      for (int j = 0; j < 4; ++j) {
+        // (A position past rec2 can only come from a tile that probe1 left
+        // unprocessed after a copy timeout, which sets the error word.)
+        const uint32_t b = uint32_t(j) >= vc[u]       ? 0u
+                           : ls[j] >= kSettled        ? (ls[j] & 0xFFu)
+                           : ls[j] < sb.rec2_len      ? uint32_t(sb.f2[ls[j]])
+                                                      : 0u;
+        w |= b << (8 * j);
+      }
+      f1w[q[u]] = w;
     }
   }
 }

@@ -58,14 +58,16 @@ struct SliceBufs {
   uint32_t shift;     // slice of bucket j = j >> shift
   uint64_t cap1;      // rec1 records per slice, a multiple of 256 (the spill region follows)
   uint64_t cap2;      // rec2 records per slice (the spill region follows)
+  uint64_t rec2_len;  // S * cap2 + n: records rec2 and f2 hold
   uint32_t* fill1;    // [(S + 1) * 32] rec1 records claimed per slice, then the
                       // spill count (one counter per 128-byte line)
   uint32_t* fill2;    // [(S + 3) * 32] rec2 records claimed per slice, then
                       // the spill count and two tile counters
   uint32_t* dst;      // [n]     rec1 position of key j
   uint64_t* rec1;     // [S * cap1 + n] key hashes grouped by the slice of i1
-  uint8_t* f1;        // [S * cap1 + n] result of probe1 (kPending: see link / f2)
-  uint32_t* link;     // [S * cap1 + n] rec2 position of a pending rec1 record
+  uint8_t* f1;        // [S * cap1 + n] flag of each rec1 record (written by merge)
+  uint32_t* link;     // [S * cap1 + n] rec2 position of a pending rec1 record,
+                      // else its flag tagged kSettled
   uint64_t* rec2;     // [S * cap2 + n] pending records grouped by i2's slice
   uint8_t* f2;        // [S * cap2 + n] result of probe2 / the eviction loop
 };
