@@ -222,9 +222,10 @@ def slice_kernel_bytes(phases: dict, W, chunk: int) -> dict:
         sweep = tb * (1 if op == "query" else 2) * passes
         pf = max(0.0, pend[op])
         out["slice_split"] += n * (8 + 8 + 4)  # key read, rec1 write, dst write
-        out["slice_probe1"] += n * (8 + 1 + pf * (8 + 4)) + sweep
-        out["slice_probe2"] += n * pf * (8 + 1) + sweep
-        out["slice_merge"] += n * (2 + pf * (4 + 1) + 4 + 1 + 1)
+        out["slice_probe1"] += n * (8 + 4 + pf * 8) + sweep  # rec1, link, rec2
+        out["slice_probe2"] += n * pf * (8 + 1) + sweep         # rec2, f2
+        # merge: link, f2 of pending records, f1; out: dst, f1, flag
+        out["slice_merge"] += n * (4 + pf * 1 + 1 + 4 + 1 + 1)
     return out
 
 

@@ -483,7 +483,10 @@ constexpr int ROUND_CONTINUE = -1;
 // inserted into its alternate bucket, using the words the probe loaded.  If
 // that bucket lost its room meanwhile, the evicted tag stays in hand and
 // the chain goes on from there.  A tag is never duplicated or lost; run by
-// one thread, both orders leave the same table.
+// one thread, both orders leave the same table.  The evicted tag's bucket
+// is the chosen candidate's alternate bucket, which the probe has just
+// loaded: its words serve the next step (a stale word only costs the CAS
+// that detects it), so no round reloads it.
 //
 // FW alternate buckets (the frontier) are probed together per group,
 // groups in candidate order; the choice does not depend on FW.
@@ -528,6 +531,9 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
         tb = ab[q];
       }
     }
+    // No bucket open after the last group: the swap goes to the last
+    // candidate, whose alternate bucket's words are ab[FW - 1].
+    if (!open && g + FW == H) tb = ab[FW - 1];
   }
   // Swap the new tag into the chosen slot.
   const uint32_t sl = (start + uint32_t(chosen)) & (G::B - 1);
@@ -556,7 +562,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   uint32_t moved;
   c.cur = alt_of<G>(d, c.cur, evicted, moved);
   c.tag = moved;
-  if (open && evicted == t[chosen])
+  if (cand[chosen] && evicted == t[chosen])
     c.bk = tb;  // the probe's words of that very bucket
   else
     c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
