@@ -142,6 +142,7 @@ __device__ __forceinline__ Bucket<G> load_bucket(const typename G::Word* p) {
 #ifndef CF_EVICT_L2_64B
 #define CF_EVICT_L2_64B 0
 #endif
+
 template <class G>
 __device__ __forceinline__ Bucket<G> load_bucket_ev(const typename G::Word* p) {
   if constexpr (CF_EVICT_L2_64B && G::kWpb == 1) {
@@ -635,6 +636,27 @@ __device__ __forceinline__ Chain<G> chain_start(const DevFilter& d,
   c.tag = first ? kh.fp : (kh.fp | G::kChoice);
   c.ev = 0;
   c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
+  return c;
+}
+
+// The bucket chain_start loads for this key.
+template <class G>
+__device__ __forceinline__ uint64_t chain_first_bucket(const KeyHash& kh) {
+  uint64_t rng = kh.h;
+  return (rng_next(rng) & 1) == 0 ? kh.i1 : kh.i2;
+}
+
+// chain_start with that bucket's words loaded beforehand.
+template <class G>
+__device__ __forceinline__ Chain<G> chain_start_loaded(const KeyHash& kh,
+                                                       const Bucket<G>& bk) {
+  Chain<G> c;
+  c.rng = kh.h;
+  const bool first = (rng_next(c.rng) & 1) == 0;
+  c.cur = first ? kh.i1 : kh.i2;
+  c.tag = first ? kh.fp : (kh.fp | G::kChoice);
+  c.ev = 0;
+  c.bk = bk;
   return c;
 }
 

@@ -36,6 +36,12 @@ constexpr int kBlock = 256;
 #ifndef CF_MINB_EVICT
 #define CF_MINB_EVICT 1
 #endif
+// The eviction loop prepares each lane's next chain while the current one
+// runs (1) or starts every chain from its queue entry when the lane is free
+// (0).
+#ifndef CF_EVICT_PREP
+#define CF_EVICT_PREP 1
+#endif
 // BFS frontier width of the single-filter eviction kernel: the number of
 // candidates whose alternate buckets are loaded together (CF_EVICT_FW; 0 or
 // an invalid value means b/2, all at once).
@@ -461,6 +467,14 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
 // trip separates the two phases; the last block to finish resets the queue.
 // FROM_HASH: keys[] holds the keys' 64-bit hashes instead of the keys (the
 // slice-partitioned path queues positions of its hash records).
+//
+// A chain's start costs three dependent loads (queue entry, key, first
+// bucket), about as long as a round or two.  So each lane prepares its next
+// chain while the current one runs, one stage per iteration, every stage
+// using what the previous iteration loaded: take and load the queue entry,
+// load the key, load the first bucket.  When the chain ends, the next one
+// starts from the prepared words at once.  (The words may be a few rounds
+// old: a stale word only costs the CAS that detects it.)
 template <class G, bool FROM_HASH = false>
 __global__ void __launch_bounds__(kBlock, CF_MINB_EVICT)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
@@ -477,27 +491,49 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
   Chain<G> c{};
   uint32_t idx = 0;
   bool active = false;
+  // The lane's next chain: stage 0 none, 1 queue entry pidx loading, 2 key
+  // pkey loading, 3 its first bucket pbk loading.
+  uint32_t pst = 0, pidx = 0;
+  uint64_t pkey = 0;
+  Bucket<G> pbk{};
+  auto key_hash = [&](uint64_t k) {
+    return FROM_HASH ? hash_full_from_h<G>(d, k) : hash_key<G>(d, k);
+  };
   for (;;) {
+    if (CF_EVICT_PREP && pst == 2 && d.max_ev != 0) {
+      pbk = load_bucket_ev<G>(bucket_ptr<G>(d, chain_first_bucket<G>(key_hash(pkey))));
+      pst = 3;
+    } else if (CF_EVICT_PREP && pst == 1) {
+      pkey = keys[pidx];
+      pst = 2;
+    }
     if (next < end) {
-      const unsigned need = __ballot_sync(0xFFFFFFFFu, !active);
-      if (!active) {
+      const bool want = pst == 0 && (CF_EVICT_PREP || !active);
+      const unsigned need = __ballot_sync(0xFFFFFFFFu, want);
+      if (want) {
         const uint32_t e = next + __popc(need & ((1u << lane) - 1u));
         if (e < end) {
-          idx = queue[e];
-          const KeyHash kh = FROM_HASH ? hash_full_from_h<G>(d, keys[idx])
-                                       : hash_key<G>(d, keys[idx]);
-          if (d.max_ev == 0) {
-            log_victim(d, kh.fp, kh.i1);
-            if (flags) st_flag(flags + idx, EV_FAIL);
-            if (evout) evout[idx] = 0;
-            n_fail++;
-          } else {
-            c = chain_start<G>(d, kh);
-            active = true;
-          }
+          pidx = queue[e];
+          pst = 1;
         }
       }
       next += __popc(need);
+    }
+    if (!active && pst != 0) {
+      if (pst == 1) pkey = keys[pidx];  // nothing to overlap these loads with
+      const bool pst3 = pst == 3;
+      idx = pidx;
+      pst = 0;
+      const KeyHash kh = key_hash(pkey);
+      if (d.max_ev == 0) {
+        log_victim(d, kh.fp, kh.i1);
+        if (flags) st_flag(flags + idx, EV_FAIL);
+        if (evout) evout[idx] = 0;
+        n_fail++;
+      } else {
+        c = pst3 ? chain_start_loaded<G>(kh, pbk) : chain_start<G>(d, kh);
+        active = true;
+      }
     }
     if (!__any_sync(0xFFFFFFFFu, active)) {
       if (next >= end) break;
