@@ -696,9 +696,9 @@ inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
 }
 
 // Grid of the eviction kernel: CF_EVICT_BPSM blocks per SM (0: as many as
-// fit).  Its chains are bound by the DRAM random-access rate, and more
-// chains in flight only add queueing (2^28-bucket workload, eviction ms per
-// step at 1 / 2 / 3 / 4 / 5 blocks per SM: 65.6 / 61.2 / 62.5 / 63.2 / 68.8).
+// fit).  Its chains are bound by dependent random accesses, and more chains
+// in flight only add queueing (2^28-bucket workload, eviction ms per step
+// at 1 / 2 / 3 / 4 / 6 blocks per SM: 58.0 / 46.2 / 48.3 / 48.8 / 48.7).
 #ifndef CF_EVICT_BPSM
 #define CF_EVICT_BPSM 2
 #endif
