@@ -380,13 +380,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
   uint32_t t0 = s_next_p, tcnt = s_next_cnt;
   uint32_t parity = 0;
   while (tcnt) {
-    if (!mbar_wait(&s_bar, parity)) {
-      // The copy did not complete: report it and leave this tile (its
-      // records stay unprocessed; the error bit tells the caller).
-      if (threadIdx.x == 0) atomicOr(&d.ctrl->error_word, kErrAsyncCopy);
-      mbar_wait(&s_bar, parity);  // once more (bounded) for the copy in flight
-      break;
-    }
+    const bool copy_ok = mbar_wait(&s_bar, parity);
     parity ^= 1u;
     // Record i of this thread: tile index loc(i) = i*kBlock + thread (lane-
     // strided: conflict-free reads of the staged tile, coalesced stores),
@@ -402,7 +396,15 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
     }
     for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) s_cnt[s] = 0;
     if (threadIdx.x == 32) s_spilled = 0;
-    __syncthreads();  // pref consumed, counters zeroed
+    // pref consumed, counters zeroed; the block leaves together if any of
+    // its threads gave up on the copy.
+    if (!__syncthreads_and(copy_ok)) {
+      // The copy did not complete: report it and leave this tile (its
+      // records stay unprocessed; the error bit tells the caller).
+      if (threadIdx.x == 0) atomicOr(&d.ctrl->error_word, kErrAsyncCopy);
+      mbar_wait(&s_bar, parity ^ 1u);  // once more (bounded) for the copy in flight
+      break;
+    }
     if (threadIdx.x == 0) fetch();
     uint32_t slrk[N];  // slice << 16 | rank of a pending record, else kSettled | flag
 #pragma unroll
@@ -497,8 +499,10 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
 
 // ---------------------------------------------------------------------------
 // probe2: the operation on bucket i2 for the rec2 records, slice regions in
-// order, then the spill region.  Warp tiles of 32*K positions; positions
-// past a region's fill are skipped.
+// order, then the spill region.  The filled parts of the regions are
+// numbered consecutively (a prefix of their fills in shared memory), and
+// block tiles of kBlock*8 of those numbers are handed out in order by a
+// counter, so that only records are visited.
 // ---------------------------------------------------------------------------
 template <class G, int OP, int K>
 __global__ void __launch_bounds__(kBlock, CF_SLICE2_MINB)
