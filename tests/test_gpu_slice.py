@@ -112,17 +112,18 @@ def test_sliced_insert_invariants(cf, f, b, policy, eviction):
     assert st["insert_fail"] <= int((ofl == 0).sum()) + max(5, n // 100)
 
 
-def test_sliced_insert_in_several_batches_then_query_and_delete(cf):
-    """The benchmark's protocol on 2^16 buckets with the sliced path forced:
-    fill 0 -> 0.5 -> 0.8 -> 0.95 in three calls, query all keys plus
-    negatives, delete half; every step checked as on the plain path."""
-    m, f, b = 1 << 16, 16, 4
+def _fill_query_delete(cf, m, f, b, slice_bytes):
+    """The benchmark's protocol with the sliced path forced: fill 0 -> 0.5
+    -> 0.8 -> 0.95 in three calls, query all keys plus negatives, delete
+    half; every step checked as on the plain path."""
     w = workloads.Workload("t", m, f, b, 500, 2, (0.5, 0.8, 0.95), 0, 0, 0)
     ks = workloads.keys(2, w.n_insert)
-    g = _sliced(cf.CuckooFilter(m, f, b, 500), slice_bytes=8192)
+    g = _sliced(cf.CuckooFilter(m, f, b, 500), slice_bytes=slice_bytes)
+    g.set_kernel_timing(True)
     o = oracle.OracleFilter(m, f, b, 500)
     flags = np.concatenate([g.insert(to_dev(ks[lo:hi])).cpu().numpy()
                             for lo, hi in w.insert_segments()])
+    assert _ran_sliced(g)
     st = _check_parallel_insert(cf, g, o, ks, flags, f, b, "xor", m)
     assert st["insert_fail"] <= 5
     neg = workloads.keys(2, 1 << 18, start=ks.size)
@@ -142,6 +143,20 @@ def test_sliced_insert_in_several_batches_then_query_and_delete(cf):
                             oracle_flags=ofl)
     assert probs == [], probs
     assert g.stats()["occupancy"] == g.count_occupied()
+    assert g.stats()["error_word"] == 0
+
+
+def test_sliced_insert_in_several_batches_then_query_and_delete(cf):
+    """2^16 buckets in slices of 8 KiB (64 slices)."""
+    _fill_query_delete(cf, 1 << 16, 16, 4, 8192)
+
+
+@pytest.mark.parametrize("f,b", [(16, 4), (16, 8)])
+def test_sliced_at_the_maximum_slice_count(cf, f, b):
+    """Slices of one bucket's size ask for more slices than the maximum:
+    the table gets 1024 slices of 64 buckets, the largest shared-memory
+    footprint of the split and bucket passes."""
+    _fill_query_delete(cf, 1 << 16, f, b, f * b // 8)
 
 
 def test_sliced_spill_with_duplicates(cf):
