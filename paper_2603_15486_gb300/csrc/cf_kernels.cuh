@@ -31,6 +31,18 @@ constexpr int kBlock = 256;
 #ifndef CF_MINB_MUT
 #define CF_MINB_MUT 2
 #endif
+// The same for tables that L2 holds (at most kL2TableBytes): their CAS round
+// trips end in L2, and more warps in flight pay (2^22 slots, ms per insert /
+// delete of 0.95 * 2^22 keys at 2 -> 4 blocks per SM: f16 b16 0.259 / 0.166
+// -> 0.230 / 0.133, f16 b4 0.516 / 0.203 -> 0.505 / 0.150, f8 b8 0.236 /
+// 0.237 -> 0.223 / 0.185).  16-byte buckets keep CF_MINB_MUT: with four
+// keys of two words each per thread, 64 registers spill and they got
+// slower (f16 b8 0.237 -> 0.267 ms per insert).  DRAM-resident tables keep
+// it too (plain large workload 160.7 -> 169.6 ms per step at 4).
+#ifndef CF_MINB_MUT_L2
+#define CF_MINB_MUT_L2 4
+#endif
+constexpr uint64_t kL2TableBytes = 64ull << 20;
 // Minimum resident blocks per SM requested for the eviction kernel (its
 // chains are latency-bound: more resident warps, more chains in flight).
 #ifndef CF_MINB_EVICT
@@ -439,8 +451,8 @@ __device__ __forceinline__ int evict_one(const DevFilter& d, uint64_t key,
 // ---------------------------------------------------------------------------
 // Single-filter kernels: a persistent grid walks the batch's tiles.
 // ---------------------------------------------------------------------------
-template <class G, int K>
-__global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
+template <class G, int K, int MINB = CF_MINB_MUT>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
                 uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
                 uint32_t* __restrict__ queue) {
@@ -632,8 +644,8 @@ k_contains(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
     tile_contains<G, K>(d, keys, n, base, lane, flags);
 }
 
-template <class G, int K>
-__global__ void __launch_bounds__(kBlock, CF_MINB_MUT)
+template <class G, int K, int MINB = CF_MINB_MUT>
+__global__ void __launch_bounds__(kBlock, MINB)
 k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
          uint8_t* __restrict__ flags) {
   const uint32_t lane = threadIdx.x & 31;
@@ -731,6 +743,9 @@ template <class G>
 struct Launch {
   static constexpr int KQ = Tiles<G, false>::K;
   static constexpr int KM = Tiles<G, true>::K;
+  // Resident blocks of the mutating kernels for an L2-resident table.
+  static constexpr int MINB_L2 = G::kBucketBytes == 16 ? CF_MINB_MUT : CF_MINB_MUT_L2;
+  static bool l2_table(const DevFilter& d) { return d.m * G::kBucketBytes <= kL2TableBytes; }
 
   static cudaError_t contains(const DevFilter& d, const uint64_t* keys,
                               uint64_t n, uint8_t* flags, cudaStream_t s,
@@ -744,7 +759,7 @@ struct Launch {
   static cudaError_t remove(const DevFilter& d, const uint64_t* keys,
                             uint64_t n, uint8_t* flags, cudaStream_t s,
                             KernelTimer* t) {
-    auto fn = k_remove<G, KM>;
+    auto fn = l2_table(d) ? k_remove<G, KM, MINB_L2> : k_remove<G, KM>;
     if (t) t->begin(KK_REMOVE, s);
     fn<<<persistent_grid(fn, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags);
     if (t) t->end(KK_REMOVE, s);
@@ -754,7 +769,7 @@ struct Launch {
                                   uint32_t n, uint8_t* flags, uint32_t* evout,
                                   uint32_t* queue, cudaStream_t s,
                                   KernelTimer* t) {
-    auto f1 = k_insert_direct<G, KM>;
+    auto f1 = l2_table(d) ? k_insert_direct<G, KM, MINB_L2> : k_insert_direct<G, KM>;
     if (t) t->begin(KK_INSERT_DIRECT, s);
     f1<<<persistent_grid(f1, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags,
                                                              evout, queue);
