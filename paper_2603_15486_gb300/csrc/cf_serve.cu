@@ -157,7 +157,9 @@ bool admit(cf_server* s) {
   bool any = false;
   while (!s->admission.empty()) {
     FSlot* fs = s->filters[s->admission.front()];
-    if (fs->state != CF_FILTER_PENDING || fs->remove_requested) {
+    // A filter removed before admission still runs the requests queued for
+    // it (it closes after them); with none queued it closes unallocated.
+    if (fs->state != CF_FILTER_PENDING || (fs->remove_requested && fs->q.empty())) {
       s->admission.pop_front();
       continue;
     }

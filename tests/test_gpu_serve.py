@@ -134,6 +134,34 @@ def test_admission_waits_for_budget(cf):
     srv.close()
 
 
+def test_removed_pending_filter_still_runs_its_requests(cf):
+    """A filter removed before the budget admitted it keeps its queued
+    requests: it is admitted when room frees up, runs them, then closes.
+    A pending filter removed with nothing queued closes unallocated."""
+    m = 1 << 16
+    one = cf.required_bytes(num_buckets=m, fp_bits=16, slots_per_bucket=4)
+    srv = cf.Server(int(1.5 * one), max_inflight=2, max_wave_items=8, max_wave_keys=1 << 16)
+    a, b, c = (srv.add_filter(m) for _ in range(3))
+    ks = torch.from_numpy(workloads.keys(6, 40000).view(np.int64)).cuda()
+    srv.submit(a, "insert", ks)
+    srv.submit(b, "insert", ks)
+    out_b = torch.zeros(40000, dtype=torch.uint8, device="cuda")
+    srv.submit(b, "contains", ks, out_b)
+    srv.remove_filter(b)                 # pending, two requests queued
+    srv.remove_filter(c)                 # pending, nothing queued
+    assert srv.drain(300) == 4           # b waits for a's budget
+    assert srv.filter_state(b) == "pending"
+    srv.remove_filter(a)
+    assert srv.drain(60000) == 0
+    assert srv.filter_state(a) == "closed"
+    assert srv.filter_state(b) == "closed" and srv.filter_state(c) == "closed"
+    assert out_b.cpu().numpy().all()
+    done = srv.poll()
+    assert len(done) == 3 and (done["status"] == 0).all()
+    assert srv.stats()["used_bytes"] == 0
+    srv.close()
+
+
 def test_watchdog_marks_late_waves(cf):
     srv = cf.Server(1 << 30, max_inflight=2, max_wave_items=8, max_wave_keys=1 << 20,
                     watchdog_us=1)
