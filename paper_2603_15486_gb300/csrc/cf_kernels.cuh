@@ -43,10 +43,13 @@ constexpr int kBlock = 256;
 #define CF_MINB_MUT_L2 4
 #endif
 constexpr uint64_t kL2TableBytes = 64ull << 20;
-// Minimum resident blocks per SM requested for the eviction kernel (its
-// chains are latency-bound: more resident warps, more chains in flight).
+// Minimum resident blocks per SM requested for the eviction kernel: 2, the
+// grid's own blocks per SM (evict_grid), so that every geometry fits them;
+// only f32 b16 needed the cap (159 -> 128 registers, a few spilled): on a
+// 256 MiB table its eviction loop went from 1.23 to 1.06 ms (BFS) and from
+// 1.90 to 1.48 ms (DFS) per fill to LF 0.95.
 #ifndef CF_MINB_EVICT
-#define CF_MINB_EVICT 1
+#define CF_MINB_EVICT 2
 #endif
 // The eviction loop prepares each lane's next chain while the current one
 // runs (1) or starts every chain from its queue entry when the lane is free
