@@ -183,7 +183,7 @@ cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk);
  * the interleaving of keys differs, so query flags are identical and insert
  * / delete results satisfy the same invariants (which keys win a contended
  * bucket may differ, as between any two concurrent runs).
- *  - mode: 0 never, 1 automatic (the default: tables of at least 512 MiB and
+ *  - mode: 0 never, 1 automatic (the default: tables of at least 256 MiB and
  *    batches of at least num_buckets / 8 keys), 2 always.
  *  - slice_bytes: table bytes per slice, rounded down to a power-of-two
  *    number of buckets (0: 32 MiB).  At most 1024 slices: larger tables get

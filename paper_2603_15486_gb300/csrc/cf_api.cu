@@ -36,7 +36,7 @@ constexpr uint64_t kInsertChunk = 1ull << 28;  // keys per insert launch pair
 constexpr uint64_t kSliceBytes = 32ull << 20;
 constexpr uint64_t kSliceChunk = 1ull << 28;   // keys per sliced pass
 constexpr uint64_t kSliceChunkMax = 1ull << 30;
-constexpr uint64_t kSliceAutoTable = 512ull << 20;
+constexpr uint64_t kSliceAutoTable = 256ull << 20;
 constexpr uint32_t kDefaultVictims = 4096;
 constexpr uint32_t kMaxVictims = 1u << 26;
 
