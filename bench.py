@@ -792,6 +792,118 @@ def serve_arm(args):
 # ---------------------------------------------------------------------------
 # Ablations of the paper's Sec. 5.4 on the paper's geometry (f16, b = 16).
 # ---------------------------------------------------------------------------
+def sweep_arm(args):
+    """The parameter sweep: fingerprint bits 8 / 16 / 32 x slots 4 / 8 / 16
+    on 2^26 buckets, each filled from empty in steps to load factors 0.90,
+    0.92, 0.94, 0.96 and 0.98 with distinct keys from [0, 2^32); after each
+    step the step's insert rate, failures and eviction-depth percentiles,
+    then the query rate of 2^24 stored keys and of 2^24 negatives from
+    [2^32, 2^64) with their false-positive rate against Eq. 4 (the paper's
+    FPR protocol, Sec. 5.3).  Then Zipf(1.1)-duplicated keys filled to LF
+    0.95 on 2^22 buckets for two geometries.  Per-key eviction counts take
+    the plain kernels."""
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2603_15486_gb300 import CuckooFilter
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1)
+
+    def eq4(f, b, alpha):  # Eq. 4 with fingerprints 1 .. 2^f - 1
+        return 1.0 - (1.0 - 1.0 / (2.0 ** f - 1.0)) ** (2.0 * b * alpha)
+
+    m = 1 << 26
+    lfs = (0.90, 0.92, 0.94, 0.96, 0.98)
+    nq = 1 << 24
+    neg = torch.empty(nq, dtype=torch.int64, device="cuda")
+    workloads.high_keys_dev(neg.data_ptr(), nq, 8, 0, sh)
+    qout = torch.empty(nq, dtype=torch.uint8, device="cuda")
+    geoms = []
+    for f in (8, 16, 32):
+        for b in (4, 8, 16):
+            nmax = workloads.lf_count(m, b, lfs[-1])
+            keys = torch.empty(nmax, dtype=torch.int64, device="cuda")
+            workloads.low32_keys_dev(keys.data_ptr(), nmax, 3, 0, sh)
+            stream.synchronize()
+            g = CuckooFilter(m, f, b, 500)
+            lo, pts = 0, []
+            for a in lfs:
+                hi = workloads.lf_count(m, b, a)
+                fl = torch.empty(hi - lo, dtype=torch.uint8, device="cuda")
+                evc = torch.empty(hi - lo, dtype=torch.int32, device="cuda")
+                t_ins = timed(lambda: g.insert(keys[lo:hi], flags=fl, evictions=evc,
+                                               stream=stream))
+                e = evc.cpu().numpy()
+                fails = int((fl != 1).sum())
+                npos = min(nq, hi)
+                if not pts:  # untimed first query (first-launch setup on the host)
+                    g.contains(keys[:npos], out=qout[:npos], stream=stream)
+                t_qp = timed(lambda: g.contains(keys[:npos], out=qout[:npos], stream=stream))
+                found = int(qout[:npos].sum())
+                t_qn = timed(lambda: g.contains(neg, out=qout, stream=stream))
+                fp = int(qout.sum())
+                alpha = g.stats(stream=stream)["occupancy"] / (m * b)
+                pts.append({"lf": a, "insert_mops": round((hi - lo) / t_ins / 1e3, 1),
+                            "inserted": hi - lo, "fails": fails,
+                            "evictions_p50_p90_p95_p99_max": [int(np.percentile(e, q))
+                                                              for q in (50, 90, 95, 99)]
+                            + [int(e.max())],
+                            "query_pos_mops": round(npos / t_qp / 1e3, 1),
+                            "query_pos_found": found, "query_pos": npos,
+                            "query_neg_mops": round(nq / t_qn / 1e3, 1),
+                            "fpr": fp / nq, "fpr_eq4": round(eq4(f, b, alpha), 8)})
+                lo = hi
+            g.close()
+            del keys
+            geoms.append({"f": f, "b": b, "table_bytes": m * b * f // 8, "points": pts})
+    # Zipf(1.1)-duplicated keys (a universe of as many distinct keys as the
+    # fill), filled to LF 0.95 in one call: failures and victims, no
+    # assertion of zero (copies of a key beyond the 2b its two buckets hold
+    # each run the eviction loop to max_evictions and fail).
+    mz = 1 << 22
+    zipf = []
+    for f, b in ((16, 4), (16, 16)):
+        n = workloads.lf_count(mz, b, 0.95)
+        zk = torch.from_numpy(workloads.zipf_keys(n, n).view(np.int64)).to("cuda")
+        g = CuckooFilter(mz, f, b, 500, victim_capacity=1 << 20)
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        evc = torch.empty(n, dtype=torch.int32, device="cuda")
+        t = timed(lambda: g.insert(zk, flags=fl, evictions=evc, stream=stream))
+        st = g.stats(stream=stream)
+        e = evc.cpu().numpy()
+        zipf.append({"f": f, "b": b, "buckets": mz, "keys": n,
+                     "insert_mops": round(n / t / 1e3, 1), "fails": int((fl != 1).sum()),
+                     "victims": st["victims"],
+                     "evictions_p50_p90_p95_p99_max": [int(np.percentile(e, q))
+                                                       for q in (50, 90, 95, 99)]
+                     + [int(e.max())]})
+        g.close()
+        del zk
+    return {"metric": "parameter sweep: insert / query Mops/s, eviction depth and FPR by "
+                      "fingerprint bits, slots and load factor",
+            "mode": "sweep", "unit": "Mops/s", "n_gpus": 1, "higher_is_better": True,
+            "value": next(p["insert_mops"] for gm in geoms if gm["f"] == 16 and gm["b"] == 16
+                          for p in gm["points"] if p["lf"] == 0.96),
+            "config": {"workload": "sweep_2^26 (f 8/16/32 x b 4/8/16, LF 0.90-0.98)",
+                       "buckets": m, "keys": "distinct low32 (seed 3); negatives high "
+                       "(seed 8); Zipf(1.1) over a universe of n keys (rank seed 33)",
+                       "negatives": nq, "value_is": "f16 b16 insert Mops/s of the step "
+                       "to LF 0.96"},
+            "geometries": geoms, "zipf": zipf}
+
+
 def ablation_arm(args):
     import numpy as np
     import torch
@@ -959,7 +1071,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation", "probe"],
+    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation", "probe", "sweep"],
                     default="main",
                     help="main: the large-filter headline; batched / serve: the "
                          "many-filters and serving workloads (one JSON line each)")
@@ -994,6 +1106,8 @@ def main(argv=None):
         out = serve_arm(args)
     elif args.mode == "ablation":
         out = ablation_arm(args)
+    elif args.mode == "sweep":
+        out = sweep_arm(args)
     elif args.mode == "probe":
         out = probe_arm(args)
     else:
