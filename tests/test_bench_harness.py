@@ -67,6 +67,34 @@ def test_bytes_per_op_model():
     assert b64["query"] == 1.5 * 64 + 9
 
 
+def test_slice_stream_byte_model():
+    """Per-pass stream bytes of the sliced path, worked by hand for a table
+    of 1000 bytes and one call per operation: 100 inserts (half pending
+    after their first bucket), 200 queries (a quarter pending), 50 deletes
+    (none pending), passes of at most 64 keys."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class W:
+        table_bytes = 1000
+        n_queries, n_deletes = 200, 50
+
+        def insert_segments(self):
+            return [(0, 100)]
+
+    ph = {"insert": {"ops": 100, "direct_reads": 150},
+          "query": {"ops": 200, "bucket_reads": 250},
+          "delete": {"ops": 50, "bucket_reads": 50}}
+    got = bench.slice_kernel_bytes(ph, W(), 64)
+    # passes: insert 2, query 4, delete 1; sweeps: read once for queries,
+    # read and written back for insert and delete.
+    sweep = 1000 * (2 * 2 + 1 * 4 + 2 * 1)
+    assert got["slice_split"] == 350 * 20
+    assert got["slice_probe1"] == 100 * (12 + 0.5 * 8) + 200 * (12 + 0.25 * 8) + 50 * 12 + sweep
+    assert got["slice_probe2"] == 100 * 0.5 * 9 + 200 * 0.25 * 9 + sweep
+    assert got["slice_merge"] == 100 * (11 + 0.5) + 200 * (11 + 0.25) + 50 * 11
+
+
 def test_reference_arm_prints_one_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl",
                         "reference", "--steps", "1", "--warmup", "0"],
