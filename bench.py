@@ -488,6 +488,22 @@ def e2e_run(filt, keys, queries, W, args, stream):
     hq.copy_(queries)
     segs = W.insert_segments()
     filt.set_staging_chunk(args.e2e_chunk)
+    # This machine's host-to-device link, measured outside the timed region
+    # (four back-to-back copies of up to 1 GiB of the pinned keys), for
+    # reading E beside it.
+    nb = min(hk.numel(), 1 << 27)
+    dev = torch.empty(nb, dtype=torch.int64, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        dev.copy_(hk[:nb], non_blocking=True)
+        e0.record(stream)
+        for _ in range(4):
+            dev.copy_(hk[:nb], non_blocking=True)
+        e1.record(stream)
+    stream.synchronize()
+    link_gbps = 4 * 8 * nb / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del dev
 
     def step():
         filt.clear(stream=stream)
@@ -513,6 +529,7 @@ def e2e_run(filt, keys, queries, W, args, stream):
             "steps": args.e2e_steps, "pinned": pinned,
             "ms_per_step": round(el / args.e2e_steps * 1e3, 3),
             "staging_chunk": args.e2e_chunk,
+            "h2d_link_GBps": round(link_gbps, 1),
             "api": "cf_insert_host / cf_contains_host / cf_remove_host"}
 
 
