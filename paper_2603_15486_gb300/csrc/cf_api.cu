@@ -409,9 +409,9 @@ cf_status device_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
   return mark(f, s);
 }
 
-// Host-buffer form: two staging slots; H2D of chunk c+1 (stream s_in)
-// overlaps the kernels of chunk c (the caller's stream) and the D2H of
-// chunk c-1's flags (stream s_out).
+// Host-buffer form: kStageSlots staging slots; the H2D copies of the next
+// chunks (stream s_in) overlap the kernels of chunk c (the caller's stream)
+// and the D2H of earlier chunks' flags (stream s_out).
 cf_status host_op(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
                   uint8_t* flags_h, void* stream) {
   if (!f) return CF_EINVAL;
@@ -429,10 +429,10 @@ cf_status host_op(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
   const uint64_t chunk = f->stage_chunk;
   const uint64_t nchunks = (n + chunk - 1) / chunk;
   for (uint64_t c = 0; c < nchunks; ++c) {
-    Stage& sg = f->stage[c & 1];
+    Stage& sg = f->stage[c % cfk::kStageSlots];
     const uint64_t off = c * chunk;
     const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
-    if (c >= 2) CF_CUDA(cudaStreamWaitEvent(f->s_in, sg.out_done, 0));
+    if (c >= cfk::kStageSlots) CF_CUDA(cudaStreamWaitEvent(f->s_in, sg.out_done, 0));
     CF_CUDA(cudaMemcpyAsync(sg.keys, keys_h + off, len * sizeof(uint64_t),
                             cudaMemcpyHostToDevice, f->s_in));
     CF_CUDA(cudaEventRecord(sg.in_done, f->s_in));

@@ -15,6 +15,13 @@ namespace cfk {
 // Keys per staging chunk of the host-buffer calls (default).
 constexpr uint64_t kDefaultStage = 1ull << 24;
 
+// Staging slots of the host-buffer calls: chunk c uses slot c mod
+// kStageSlots, so the copy of chunk c + kStageSlots - 1 can start while
+// chunk c runs; the host-to-device copies then follow one another without
+// waiting for flags to come back (a copy started on an idle link ran at
+// half its rate).
+constexpr int kStageSlots = 4;
+
 struct Stage {
   uint64_t* keys = nullptr;
   uint8_t* flags = nullptr;
@@ -90,7 +97,7 @@ struct cf_filter {
   uint32_t* queue = nullptr;
   uint64_t queue_cap = 0;
   uint64_t stage_chunk = cfk::kDefaultStage;
-  cfk::Stage stage[2];
+  cfk::Stage stage[cfk::kStageSlots];
   cudaStream_t s_in = nullptr, s_out = nullptr;
   bool stage_ready = false;
   cfk::FilterTimer* timer = nullptr;  // non-null while kernel timing is on
