@@ -488,9 +488,9 @@ def e2e_run(filt, keys, queries, W, args, stream):
     hq.copy_(queries)
     segs = W.insert_segments()
     filt.set_staging_chunk(args.e2e_chunk)
-    # This machine's host-to-device link, measured outside the timed region
-    # (four back-to-back copies of up to 1 GiB of the pinned keys), for
-    # reading E beside it.
+    # The host-to-device link's copy rate, measured outside the timed
+    # region (four back-to-back copies of up to 1 GiB of the pinned keys),
+    # for reading E beside it.
     nb = min(hk.numel(), 1 << 27)
     dev = torch.empty(nb, dtype=torch.int64, device="cuda")
     e0 = torch.cuda.Event(enable_timing=True)
