@@ -139,7 +139,7 @@ def hash_params(keys, m: int, f: int, policy: int = CFO_POLICY_XOR):
 
 
 def fpr_expected(f: int, b: int, alpha: float, policy: int = CFO_POLICY_XOR) -> float:
-    """Eq. 4 (Sec. 2.1) with the fingerprint alphabet of this build: the
+    """Eq. 4 (Sec. 2.1) with the fingerprint alphabet used here: the
     fingerprint is never zero, so it takes 2^f - 1 values (2^(f-1) - 1 under
     the Offset policy, whose top tag bit is the choice bit)."""
     vals = (2 ** f - 1) if policy == CFO_POLICY_XOR else (2 ** (f - 1) - 1)
