@@ -65,50 +65,54 @@ class _Stats(ctypes.Structure):
         "ins_direct_reads", "ins_direct_writes", "ins_evict_keys")]
 
 
+def bind(L):
+    """Set the ctypes signatures of an oracle library handle."""
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    L.cfo_create.restype = vp
+    L.cfo_create.argtypes = [u64, u32, u32, u32, u32, u32]
+    L.cfo_destroy.argtypes = [vp]
+    L.cfo_clear.argtypes = [vp]
+    L.cfo_xxh64_u64.restype = u64
+    L.cfo_xxh64_u64.argtypes = [u64, u64]
+    L.cfo_hash.argtypes = [vp, u64, vp, vp, vp]
+    L.cfo_alt.restype = u64
+    L.cfo_alt.argtypes = [vp, u64, u32]
+    L.cfo_insert.restype = ctypes.c_int
+    L.cfo_insert.argtypes = [vp, u64, vp]
+    L.cfo_contains.restype = ctypes.c_int
+    L.cfo_contains.argtypes = [vp, u64]
+    L.cfo_remove.restype = ctypes.c_int
+    L.cfo_remove.argtypes = [vp, u64]
+    for name in ("cfo_insert_batch",):
+        getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
+    for name in ("cfo_contains_batch", "cfo_remove_batch"):
+        getattr(L, name).argtypes = [vp, vp, u64, vp]
+    L.cfo_hash_batch.argtypes = [vp, vp, u64, vp, vp, vp]
+    L.cfo_hash_params_batch.restype = ctypes.c_int
+    L.cfo_hash_params_batch.argtypes = [u64, u32, u32, vp, u64, vp, vp, vp]
+    L.cfo_get_slot.restype = u32
+    L.cfo_get_slot.argtypes = [vp, u64, u32]
+    L.cfo_set_slot.argtypes = [vp, u64, u32, u32]
+    L.cfo_table_bytes.restype = u64
+    L.cfo_table_bytes.argtypes = [vp]
+    L.cfo_snapshot_bytes.restype = u64
+    L.cfo_snapshot_bytes.argtypes = [vp]
+    L.cfo_snapshot.restype = ctypes.c_int
+    L.cfo_snapshot.argtypes = [vp, vp, u64]
+    L.cfo_load.restype = ctypes.c_int
+    L.cfo_load.argtypes = [vp, vp, u64]
+    L.cfo_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    L.cfo_victims.restype = u64
+    L.cfo_victims.argtypes = [vp, vp, vp, u64]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB)
-            vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
-            L.cfo_create.restype = vp
-            L.cfo_create.argtypes = [u64, u32, u32, u32, u32, u32]
-            L.cfo_destroy.argtypes = [vp]
-            L.cfo_clear.argtypes = [vp]
-            L.cfo_xxh64_u64.restype = u64
-            L.cfo_xxh64_u64.argtypes = [u64, u64]
-            L.cfo_hash.argtypes = [vp, u64, vp, vp, vp]
-            L.cfo_alt.restype = u64
-            L.cfo_alt.argtypes = [vp, u64, u32]
-            L.cfo_insert.restype = ctypes.c_int
-            L.cfo_insert.argtypes = [vp, u64, vp]
-            L.cfo_contains.restype = ctypes.c_int
-            L.cfo_contains.argtypes = [vp, u64]
-            L.cfo_remove.restype = ctypes.c_int
-            L.cfo_remove.argtypes = [vp, u64]
-            for name in ("cfo_insert_batch",):
-                getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
-            for name in ("cfo_contains_batch", "cfo_remove_batch"):
-                getattr(L, name).argtypes = [vp, vp, u64, vp]
-            L.cfo_hash_batch.argtypes = [vp, vp, u64, vp, vp, vp]
-            L.cfo_hash_params_batch.restype = ctypes.c_int
-            L.cfo_hash_params_batch.argtypes = [u64, u32, u32, vp, u64, vp, vp, vp]
-            L.cfo_get_slot.restype = u32
-            L.cfo_get_slot.argtypes = [vp, u64, u32]
-            L.cfo_set_slot.argtypes = [vp, u64, u32, u32]
-            L.cfo_table_bytes.restype = u64
-            L.cfo_table_bytes.argtypes = [vp]
-            L.cfo_snapshot_bytes.restype = u64
-            L.cfo_snapshot_bytes.argtypes = [vp]
-            L.cfo_snapshot.restype = ctypes.c_int
-            L.cfo_snapshot.argtypes = [vp, vp, u64]
-            L.cfo_load.restype = ctypes.c_int
-            L.cfo_load.argtypes = [vp, vp, u64]
-            L.cfo_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
-            L.cfo_victims.restype = u64
-            L.cfo_victims.argtypes = [vp, vp, vp, u64]
-            _lib = L
+            _lib = bind(ctypes.CDLL(_LIB))
     return _lib
 
 
@@ -158,8 +162,11 @@ class OracleFilter:
     """One sequential filter.  ``m`` buckets of ``b`` slots of ``f`` bits."""
 
     def __init__(self, m: int, f: int = 16, b: int = 4, max_evictions: int = 500,
-                 policy: int = CFO_POLICY_XOR, eviction: int = CFO_EVICT_BFS):
-        self._L = lib()
+                 policy: int = CFO_POLICY_XOR, eviction: int = CFO_EVICT_BFS,
+                 library=None):
+        # `library`: another build of the oracle source bound with bind()
+        # (the tests' planted-mistake variants); default: liboracle.so.
+        self._L = library if library is not None else lib()
         self.m, self.f, self.b = int(m), int(f), int(b)
         self.max_evictions, self.policy, self.eviction = max_evictions, policy, eviction
         h = self._L.cfo_create(self.m, f, b, max_evictions, policy, eviction)
