@@ -37,13 +37,44 @@ if ROOT not in sys.path:
 
 METRIC = "insert/query/delete Mops/s at LF 0.95 vs HBM roofline; served p99 vs plain"
 
-# DRAM bytes (read + write) per launch of the filter kernels on the large
-# workload, from one ncu capture of the current kernels (1 pass: the metrics
-# dram__bytes_read.sum and dram__bytes_write.sum over the timed step of
-# `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu`; its summary and command
-# are committed with the other ncu summaries).  Must be re-taken whenever one
-# of these kernels changes.
-NCU_DRAM_BYTES_PER_LAUNCH = {"insert_evict": (143.866e9 + 20.531e9) / 5}
+# DRAM bytes (read + write) per launch of the dominant kernel come from the
+# committed ncu summary of the large workload, which records them with a
+# hash of the kernel sources they were measured on; they are reported only
+# while the sources still have that hash (else the roofline's traffic is
+# null until the capture is taken again).
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_large_2^28x4_f16_lf0.95.md")
+KERNEL_SOURCES = ("cf_types.h", "cf_device.cuh", "cf_kernels.cuh", "cf_slice.cuh",
+                  "cf_inst_f16.cu")
+
+
+def kernel_sources_sha() -> str:
+    """First 16 hex digits of the SHA-256 of the sources the single-filter
+    kernels are compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_15486_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if the summary has no figure for it or was taken on other kernel
+    sources.  The summary holds lines of the form
+    `traffic <kernel> <bytes per launch> sources <sha16>`."""
+    import re
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    sha = kernel_sources_sha()
+    for m in re.finditer(r"^traffic (\w+) ([0-9.e+]+) sources ([0-9a-f]{16})\s*$", text, re.M):
+        if m.group(1) == kernel and m.group(3) == sha:
+            return float(m.group(2))
+    return None
+
+
 SECTOR = 32
 
 
@@ -199,6 +230,7 @@ def kernel_bytes(phases: dict, bucket_bytes: int, n_insert: int, n_query: int,
     d = phases["delete"]
     return {"insert_direct": n_insert * (d_touch * spb + 9),
             "insert_evict": n_insert * (e_touch * spb + 9 * e_keys),
+            "evict_map": 0.0,  # set by the caller from the builds per step
             "contains": n_query * (q["bucket_reads"] / q["ops"] * spb + 9),
             "remove": n_delete * ((d["bucket_reads"] + d["bucket_writes"]) / d["ops"] * spb + 9)}
 
@@ -273,6 +305,7 @@ def gpu_arm(args):
     d_flags = torch.empty(W.n_deletes, dtype=torch.uint8, device=dev)
     filt = CuckooFilter(W.m, W.f, W.b, W.max_evictions)
     filt.set_slicing(args.slicing, args.slice_bytes, args.slice_chunk)
+    filt.set_eviction_map(args.evict_map)
     stream.synchronize()
 
     segs = W.insert_segments()
@@ -362,6 +395,7 @@ def gpu_arm(args):
                    "keys": "splitmix64 seed 2, uniform uint64",
                    "parallelism": f"replicas x{ws}",
                    "slicing": args.slicing, "slice_chunk": args.slice_chunk or (1 << 28),
+                   "evict_map": args.evict_map,
                    "slice_bytes": args.slice_bytes or (32 << 20),
                    "l2": "no flush: 2 GiB table and 8 GB key arrays exceed the 129 MB L2"},
         "phases": {k: {"ms": round(v * 1e3, 3),
@@ -397,6 +431,10 @@ def gpu_arm(args):
                "phases_mops": {k: round(p["ops"] / p["s"] / 1e6, 3) for k, p in phases.items()}}
     kb = kernel_bytes(phases, W.f * W.b // 8, W.n_insert, W.n_queries, W.n_deletes)
     kb.update(slice_kernel_bytes(phases, W, args.slice_chunk or (1 << 28)))
+    # The full-bucket map: each build reads the table and writes m/8 bytes
+    # (the counters restart with every step's clear, so st_end holds one
+    # step's builds).
+    kb["evict_map"] = st_end["map_builds"] * (W.table_bytes + (W.m + 31) // 32 * 4)
     peak = peaks.get("hbm_gbs") or 6800.0
     kern = {}
     for k, (launches, ms) in ktimes.items():
@@ -405,8 +443,8 @@ def gpu_arm(args):
         ach = kb[k] * args.steps / (ms / 1e3) / 1e9
         kern[k] = {"launches": launches, "avg_launch_ms": round(ms / launches, 4),
                    "total_ms_per_step": round(ms / args.steps, 3),
-                   ("stream_bytes_per_step" if k.startswith("slice") else
-                    "algorithmic_bytes_per_step"): int(kb[k]),
+                   ("stream_bytes_per_step" if k.startswith("slice") or k == "evict_map"
+                    else "algorithmic_bytes_per_step"): int(kb[k]),
                    "achieved_GBps": round(ach, 1), "frac": round(ach / peak, 4)}
     # Per operation: the method's algorithmic bytes (32 B per bucket sector
     # the oracle touches + 9 B) at the measured operation rate.
@@ -422,9 +460,12 @@ def gpu_arm(args):
                        "achieved": kern[dom]["achieved_GBps"], "peak": peak, "unit": "GB/s",
                        "frac": kern[dom]["frac"],
                        "traffic": (args.traffic if args.traffic is not None
-                                   else NCU_DRAM_BYTES_PER_LAUNCH.get(dom)
+                                   else ncu_traffic(dom)
                                    if (W.name, args.slicing) == ("large_2^28x4_f16_lf0.95", "auto")
                                    else None),
+                       "traffic_source": ("--traffic" if args.traffic is not None else
+                                          "profiles/dram_large_2^28x4_f16_lf0.95.md, kernel "
+                                          "sources " + kernel_sources_sha()),
                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
                        if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
                        "random_sector_ceiling_GBps": ceiling["GBps_32B"],
@@ -436,6 +477,15 @@ def gpu_arm(args):
     out["random_gather"] = ceiling
     out["cpu_baseline"] = cpu
     out["e2e"] = e2e
+    # The other half of the metric: served vs plain per-request calls, and
+    # many filters in one batched launch vs a loop of per-filter launches
+    # (bounded runs; outside the timed region of the headline).
+    if ws == 1 and not args.no_extras:
+        del keys, queries, ins_flags, q_flags, d_flags
+        filt.close()
+        torch.cuda.empty_cache()
+        out["served_vs_plain"] = serve_summary(args.extras_requests)
+        out["batched_vs_loop"] = batched_summary()
     return out
 
 
@@ -506,11 +556,14 @@ def e2e_run(filt, keys, queries, W, args, stream):
     del dev
 
     def step():
+        # The asynchronous host-buffer calls, back to back; the stream's
+        # synchronisation at the end of the timed region waits for the last
+        # flags to land in host memory.
         filt.clear(stream=stream)
         for lo, hi in segs:
-            filt.insert_host(hk[lo:hi], out=hf_i[lo:hi], stream=stream)
-        filt.contains_host(hq, out=hf_q, stream=stream)
-        filt.remove_host(hk[: W.n_deletes], out=hf_d, stream=stream)
+            filt.insert_host_async(hk[lo:hi], out=hf_i[lo:hi], stream=stream)
+        filt.contains_host_async(hq, out=hf_q, stream=stream)
+        filt.remove_host_async(hk[: W.n_deletes], out=hf_d, stream=stream)
 
     for _ in range(max(1, args.e2e_warmup)):
         step()
@@ -530,7 +583,11 @@ def e2e_run(filt, keys, queries, W, args, stream):
             "ms_per_step": round(el / args.e2e_steps * 1e3, 3),
             "staging_chunk": args.e2e_chunk,
             "h2d_link_GBps": round(link_gbps, 1),
-            "api": "cf_insert_host / cf_contains_host / cf_remove_host"}
+            "api": "cf_insert_host_async / cf_contains_host_async / cf_remove_host_async "
+                   "(pinned host keys in, host flags out; one stream synchronisation after "
+                   "the timed steps)",
+            "checks": {"insert_ok": int(hf_i.sum()), "query_pos_found": int(hf_q[0::2].sum()),
+                       "remove_ok": int(hf_d.sum())}}
 
 
 def load_peaks() -> dict:
@@ -575,14 +632,16 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 # Many-filters mode: plain per-filter calls vs one batched launch per phase.
 # ---------------------------------------------------------------------------
-def batched_arm(args):
+def batched_compare(steps: int, warmup: int) -> dict:
+    """Many filters: one graph-replayed batched launch per operation against
+    a loop of per-filter calls, on the 512-filter workload (median of
+    `steps` timed repetitions after `warmup`)."""
     import torch
 
     import workloads
     from paper_2603_15486_gb300 import Batch, CuckooFilter
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
     layout = workloads.multi_filter_layout()
@@ -637,7 +696,7 @@ def batched_arm(args):
 
     def timed(fn):
         ms = []
-        for i in range(args.warmup + args.steps):
+        for i in range(warmup + steps):
             clear()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -645,7 +704,7 @@ def batched_arm(args):
             fn()
             e1.record(stream)
             stream.synchronize()
-            if i >= args.warmup:
+            if i >= warmup:
                 ms.append(e0.elapsed_time(e1))
         med = statistics.median(ms)
         check = {"insert_fail": int((f_ins != 1).sum()),
@@ -666,21 +725,42 @@ def batched_arm(args):
     plain_mops, plain_ms, plain_chk = timed(plain)
     b_mops, b_ms, b_chk = timed(lambda: batched(False))
     g_mops, g_ms, g_chk = timed(lambda: batched(True))
-    return {
-        "metric": "multi-filter insert/query/delete Mops/s (one batched launch vs a loop of per-filter launches)",
-        "mode": "batched", "value": round(g_mops, 2), "unit": "Mops/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-        "config": {"workload": "512 filters, 2^8-2^22 buckets x 4 slots, f16, keys 10^2-10^6 "
-                               "log-uniform clipped to LF 0.95; insert, query (n pos + n neg), "
-                               "delete n/2", "filters": len(layout), "keys": total,
-                   "table_bytes": sum(m * 8 for m, _ in layout), "ops_per_step": ops},
-        "plain": {"mops": round(plain_mops, 2), "ms": round(plain_ms, 3), "checks": plain_chk},
-        "batched": {"mops": round(b_mops, 2), "ms": round(b_ms, 3), "checks": b_chk},
-        "graph": {"mops": round(g_mops, 2), "ms": round(g_ms, 3), "checks": g_chk},
-        "speedup_vs_plain": round(g_mops / plain_mops, 2),
-        "tuning": tune,
-        "gpu_launches_per_step": {"plain": sum(2 + 1 + 1 for _ in layout), "batched": 2 + 1 + 1},
-    }
+    for f in filters:
+        f.close()
+    return {"config": {"workload": "512 filters, 2^8-2^22 buckets x 4, f16, keys 10^2-10^6 "
+                                   "log-uniform clipped to LF 0.95; insert, query (n pos + n neg), "
+                                   "delete n/2", "filters": len(layout), "keys": total,
+                       "table_bytes": sum(m * 8 for m, _ in layout), "ops_per_step": ops},
+            "plain": {"mops": round(plain_mops, 2), "ms": round(plain_ms, 3), "checks": plain_chk},
+            "batched": {"mops": round(b_mops, 2), "ms": round(b_ms, 3), "checks": b_chk},
+            "graph": {"mops": round(g_mops, 2), "ms": round(g_ms, 3), "checks": g_chk},
+            "speedup_vs_plain": round(g_mops / plain_mops, 2),
+            "tuning": tune,
+            "gpu_launches_per_step": {"plain": sum(2 + 1 + 1 for _ in layout),
+                                      "batched": 2 + 1 + 1}}
+
+
+def batched_arm(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    r = batched_compare(args.steps, args.warmup)
+    return {"metric": "multi-filter insert/query/delete Mops/s (one batched launch vs a loop "
+                      "of per-filter launches)",
+            "mode": "batched", "value": r["graph"]["mops"], "unit": "Mops/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            **r}
+
+
+def batched_summary() -> dict:
+    """The default bench line's batched-vs-loop figures (3 timed
+    repetitions after 1)."""
+    r = batched_compare(3, 1)
+    return {"workload": r["config"]["workload"],
+            "graph_mops": r["graph"]["mops"], "plain_loop_mops": r["plain"]["mops"],
+            "speedup": r["speedup_vs_plain"],
+            "launches_per_step": r["gpu_launches_per_step"],
+            "checks_equal": r["graph"]["checks"] == r["plain"]["checks"]}
 
 
 # ---------------------------------------------------------------------------
@@ -699,9 +779,13 @@ def _lat_stats(c, n_keys):
             "errors": int(((c["status"] != 0) & (c["status"] != 4)).sum())}
 
 
-def serve_arm(args):
-    import ctypes
-
+def serve_compare(n_requests: int, rate_points, admission: bool = True, seed: int = 5):
+    """Served (continuous batching) against plain per-request calls on the
+    serving workload: saturated throughput, then Poisson arrivals at each
+    (name, fraction, of) in rate_points, the rate being fraction x the
+    saturated request rate of `of` ("served" or "plain"); p50 / p99
+    latency of both forms at each rate.  With admission, also the same
+    requests on a server whose HBM budget holds only some of the filters."""
     import numpy as np
     import torch
 
@@ -709,10 +793,9 @@ def serve_arm(args):
     from workloads.serve import materialize
     from paper_2603_15486_gb300 import CuckooFilter, Server, _lib, plain_run_trace
 
-    torch.cuda.set_device(0)
     L = _lib.load()
     stream = torch.cuda.Stream()
-    sizes, plan = workloads.serve_trace(args.serve_requests)
+    sizes, plan = workloads.serve_trace(n_requests)
     budget = 64 << 30
     srv = Server(budget, max_inflight=4, max_wave_items=512, max_wave_keys=1 << 22,
                  use_graphs=True)
@@ -743,25 +826,31 @@ def serve_arm(args):
     reset()
     p = plain_run_trace(plain, preqs, [0.0] * R, stream=stream)
     sat_plain = _lat_stats(p, n_keys)
-    cap = sat_served["req_per_s"]
+    caps = {"served": sat_served["req_per_s"], "plain": sat_plain["req_per_s"]}
     loads = {}
-    rng = np.random.default_rng(5)
-    # Loads relative to the served capacity, plus one inside the plain
-    # baseline's own capacity (where its queue does not grow without bound).
-    points = [(f"{int(f * 100)}%", f * cap) for f in (0.5, 0.8, 0.95)]
-    points.append(("80%_of_plain_capacity", 0.8 * sat_plain["req_per_s"]))
-    for name, lam in points:
+    rng = np.random.default_rng(seed)
+    for name, frac, of in rate_points:
+        lam = frac * caps[of]
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=R))
         arrivals -= arrivals[0]
         reset()
         c = srv.run_trace(sreqs, arrivals)
         reset()
         p = plain_run_trace(plain, preqs, arrivals, stream=stream)
-        loads[name] = {"rate_req_s": round(lam, 1),
-                                        "served": _lat_stats(c, n_keys),
-                                        "plain": _lat_stats(p, n_keys)}
+        loads[name] = {"rate_req_s": round(lam, 1), "served": _lat_stats(c, n_keys),
+                       "plain": _lat_stats(p, n_keys)}
     st = srv.stats()
     srv.close()
+    out = {"workload": f"{R} requests over {len(sizes)} filters "
+                       "(2^16-2^26 buckets x 4, f16), mix 1 insert : 8 query : "
+                       "1 delete, n = 2^(20u)", "requests": R, "keys": n_keys,
+           "saturated": {"served": sat_served, "plain": sat_plain,
+                         "speedup": round(sat_served["mops"] / sat_plain["mops"], 2)},
+           "poisson": loads,
+           "server": {"waves": st["waves"],
+                      "mean_wave_requests": round(st["completed"] / max(1, st["waves"]), 2)}}
+    if not admission:
+        return out
     # Admission under a small budget: the same requests, saturated, into
     # fresh filters on a server whose HBM budget holds only some of them;
     # each filter is removed right after its last request is submitted, so
@@ -784,26 +873,48 @@ def serve_arm(args):
     done2 = srv2.poll(R + 64)
     st2 = srv2.stats()
     srv2.close()
-    admission = {"hbm_budget_bytes": small,
-                 "filters_waiting_at_start": first_pending,
-                 "drain_status": rc2, "completed": int(len(done2)),
-                 "all_ok": bool(len(done2) == R and (done2["status"] == 0).all()),
-                 "ms": round(t_adm * 1e3, 1), "mops": round(n_keys / t_adm / 1e6, 1),
-                 "used_bytes_after": st2["used_bytes"]}
+    out["admission"] = {"hbm_budget_bytes": small,
+                        "filters_waiting_at_start": first_pending,
+                        "drain_status": rc2, "completed": int(len(done2)),
+                        "all_ok": bool(len(done2) == R and (done2["status"] == 0).all()),
+                        "ms": round(t_adm * 1e3, 1), "mops": round(n_keys / t_adm / 1e6, 1),
+                        "used_bytes_after": st2["used_bytes"]}
+    return out
+
+
+def serve_arm(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    pts = [(f"{int(f * 100)}%", f, "served") for f in (0.5, 0.8, 0.95)]
+    pts += [("50%_of_plain_capacity", 0.5, "plain"), ("80%_of_plain_capacity", 0.8, "plain")]
+    r = serve_compare(args.serve_requests, pts)
     return {"metric": "served p50/p99 latency and Mops/s vs plain per-request launches",
-            "mode": "serve", "value": sat_served["mops"], "unit": "Mops/s",
+            "mode": "serve", "value": r["saturated"]["served"]["mops"], "unit": "Mops/s",
             "n_gpus": 1, "higher_is_better": True,
-            "config": {"workload": f"{R} requests over {len(sizes)} filters "
-                                   "(2^16-2^26 buckets x 4, f16), mix 1 insert : 8 query : "
-                                   "1 delete, n = 2^(20u); Poisson arrivals at 50/80/95% "
-                                   "of the served capacity", "requests": R, "keys": n_keys,
-                       "hbm_budget_bytes": budget, "max_inflight_waves": 4,
+            "config": {"workload": r["workload"] + "; Poisson arrivals at 50/80/95% of the "
+                                                  "served capacity and 50/80% of the plain one",
+                       "requests": r["requests"], "keys": r["keys"],
+                       "hbm_budget_bytes": 64 << 30, "max_inflight_waves": 4,
                        "max_wave_keys": 1 << 22, "graphs": True},
-            "saturated": {"served": sat_served, "plain": sat_plain,
-                          "speedup": round(sat_served["mops"] / sat_plain["mops"], 2)},
-            "poisson": loads,
-            "admission": admission,
-            "server": {"waves": st["waves"], "mean_wave_requests": round(st["completed"] / max(1, st["waves"]), 2)}}
+            **{k: r[k] for k in ("saturated", "poisson", "admission", "server")}}
+
+
+def serve_summary(n_requests: int = 1000) -> dict:
+    """The default bench line's served-vs-plain figures: a bounded trace,
+    saturated and at Poisson rates of 50% and 80% of the plain form's
+    capacity (where the plain form keeps up)."""
+    r = serve_compare(n_requests, [("50%_of_plain_capacity", 0.5, "plain"),
+                                   ("80%_of_plain_capacity", 0.8, "plain")],
+                      admission=False)
+    out = {"workload": r["workload"],
+           "saturated_mops": {"served": r["saturated"]["served"]["mops"],
+                              "plain": r["saturated"]["plain"]["mops"]}}
+    for name, v in r["poisson"].items():
+        out[name] = {"rate_req_s": v["rate_req_s"],
+                     "served": {k: v["served"][k] for k in ("p50_ms", "p99_ms", "mops")},
+                     "plain": {k: v["plain"][k] for k in ("p50_ms", "p99_ms", "mops")}}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -1030,88 +1141,42 @@ def ablation_arm(args):
             "eviction": evict, "bucket_policy": policy}
 
 
-# ---------------------------------------------------------------------------
-# Probe mode: the random-access ceiling of this GPU's HBM.
-# ---------------------------------------------------------------------------
-FLAVOURS = ["ld.global.nc.L1::no_allocate", "ld.global.cg", "ld.global.cs", "ld.global",
-            "ld.global.lu", "ld.relaxed.gpu.global", "ld.volatile.global",
-            "ld.global.nc.L1::no_allocate.L2::64B", "ld.global.nc.L1::no_allocate.L2::256B",
-            "atom.global.or.b64 (0)"]
-
-
-def probe_arm(args):
-    import torch
-    from paper_2603_15486_gb300 import _lib
-
-    torch.cuda.set_device(0)
-    L = _lib.load()
-    st = torch.cuda.Stream()
-    sh = st.cuda_stream
-    n = args.probe_n
-    buf = torch.zeros(1 << 31, dtype=torch.uint8, device="cuda")
-    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
-
-    def timed(launch):
-        for _ in range(2):
-            assert launch(7) == 0
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        launch(9)
-        e1.record(st)
-        st.synchronize()
-        return round(n / e0.elapsed_time(e1) / 1e6, 2)
-
-    by_flavour = {FLAVOURS[fl]: timed(lambda seed, fl=fl: L.cf_probe_gather_flavour(
-        buf.data_ptr(), buf.numel(), n, fl, seed, sink.data_ptr(), sh)) for fl in range(10)}
-    by_shape = {}
-    for ab in (8, 32):
-        for lp in (4, 8, 16):
-            by_shape[f"{ab}B_x{lp}"] = timed(lambda seed, ab=ab, lp=lp: L.cf_probe_gather(
-                buf.data_ptr(), buf.numel(), n, ab, lp, seed, sink.data_ptr(), sh))
-    l2 = timed(lambda seed: L.cf_probe_gather(buf.data_ptr(), 1 << 26, n, 8, 8, seed,
-                                              sink.data_ptr(), sh))
-    # The same load forms and the atomic over a 16 MiB region (L2-resident:
-    # the rate a slice-grouped pass can reach).
-    l2_forms = {FLAVOURS[fl]: timed(lambda seed, fl=fl: L.cf_probe_gather_flavour(
-        buf.data_ptr(), 16 << 20, n, fl, seed, sink.data_ptr(), sh)) for fl in (0, 1, 9)}
-    return {"metric": "random load rate (G loads/s) over a 2 GiB buffer", "mode": "probe",
-            "unit": "G loads/s", "value": by_flavour[FLAVOURS[0]], "n_gpus": 1,
-            "higher_is_better": True, "config": {"loads": n, "buffer_bytes": 1 << 31},
-            "by_load_form": by_flavour, "by_size_and_loads_in_flight": by_shape,
-            "l2_resident_64MiB_8B_x8": l2, "l2_resident_16MiB_by_form": l2_forms}
-
-
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation", "probe", "sweep"],
+    ap.add_argument("--mode", choices=["main", "batched", "serve", "ablation", "sweep"],
                     default="main",
                     help="main: the large-filter headline; batched / serve: the "
                          "many-filters and serving workloads (one JSON line each)")
     ap.add_argument("--serve-requests", type=int, default=4000)
-    ap.add_argument("--probe-n", type=int, default=1 << 30)
     ap.add_argument("--workload", default="large_2^28x4_f16_lf0.95")
     ap.add_argument("--cpu-workload", default="scale_2^22x4_f16_lf0.95")
     ap.add_argument("--ref-workload", default="ref_2^20x4_f16_lf0.95")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the served-vs-plain and batched-vs-loop summaries")
+    ap.add_argument("--extras-requests", type=int, default=1000,
+                    help="requests of the served-vs-plain summary trace")
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-warmup", type=int, default=1)
     ap.add_argument("--e2e-chunk", type=int, default=1 << 25,
                     help="keys per staging chunk of the host-buffer calls")
     ap.add_argument("--slicing", choices=["off", "auto", "always"], default="auto",
                     help="slice-partitioned execution of the filter calls (cf_set_slicing)")
+    ap.add_argument("--evict-map", choices=["off", "auto", "always"], default="auto",
+                    help="full-bucket map of the eviction loop (cf_set_eviction_map)")
     ap.add_argument("--slice-bytes", type=int, default=0,
                     help="table bytes per slice (0: the library default, 32 MiB)")
     ap.add_argument("--slice-chunk", type=int, default=0,
                     help="keys per sliced pass (0: the library default, 2^28)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture "
-                         "(default: the committed full-size capture of the eviction loop)")
+                         "(default: the committed full-size capture, if taken on the "
+                         "current kernel sources)")
     args = ap.parse_args(argv)
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1")
@@ -1125,8 +1190,6 @@ def main(argv=None):
         out = ablation_arm(args)
     elif args.mode == "sweep":
         out = sweep_arm(args)
-    elif args.mode == "probe":
-        out = probe_arm(args)
     else:
         out = gpu_arm(args)
     if out is not None:

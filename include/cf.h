@@ -108,11 +108,20 @@ typedef struct {
                               bit 2: an asynchronous copy of the sliced
                               path timed out (its records were skipped)    */
   uint32_t victim_capacity;
+  uint64_t map_builds;     /* eviction launches that built and used the
+                              full-bucket map (cf_set_eviction_map)        */
+  uint64_t cas_retry[7];   /* CAS-retry histogram: failed CAS attempts by
+                              retry depth within one retry loop, bins 0, 1,
+                              2-3, 4-7, 8-15, 16-63, >= 64 (bin 0: a loop's
+                              first attempt failed; bin k counts loops that
+                              needed more retries than bins below k allow) */
 } cf_stats_t;
 
 /* ---- sizes ------------------------------------------------------------- */
-/* Bytes of the raw table: m * b * f / 8.  0 if the config is invalid. */
-size_t cf_table_bytes(const cf_config* cfg);
+/* Bytes of the raw table (Sec. 4.2: m buckets of b tags of f bits, packed):
+ * m * b * f / 8.  0 unless f is 8, 16 or 32, b is 4, 8 or 16 and
+ * 1 <= m <= 2^32 (the bucket policy's own rule on m is checked at create). */
+size_t cf_table_bytes(uint64_t num_buckets, uint32_t fp_bits, uint32_t slots_per_bucket);
 /* Bytes of device memory a filter needs (control block + victim log +
  * table, 256-byte aligned pieces).  0 if the config is invalid. */
 size_t cf_required_bytes(const cf_config* cfg);
@@ -120,7 +129,11 @@ size_t cf_required_bytes(const cf_config* cfg);
 size_t cf_snapshot_bytes(const cf_filter* f);
 
 /* ---- lifetime ----------------------------------------------------------- */
-/* cf_create: the library cudaMalloc's cf_required_bytes and zeroes it
+/* Sec. 4.7 describes a C-style interface over raw device pointers and batch
+ * lengths, with the parameters fixed per filter (there as compile-time
+ * template constants; here runtime arguments dispatched to the compiled
+ * instances, f x b x policy).  The calls below are that interface.
+ * cf_create: the library cudaMalloc's cf_required_bytes and zeroes it
  * (synchronous).  Uses XOR + BFS with the default victim log.
  * Errors: CF_EINVAL (parameters), CF_ENOMEM, CF_ECUDA. */
 cf_status cf_create(uint64_t num_buckets, uint32_t fp_bits,
@@ -155,11 +168,15 @@ cf_status cf_contains(cf_filter* f, const uint64_t* keys, uint64_t n,
 /* Delete keys[0..n) (Alg. 3): clears one matching tag from i1, else i2. */
 cf_status cf_remove(cf_filter* f, const uint64_t* keys, uint64_t n,
                     uint8_t* out_flags, void* stream);
-/* Zero the table and all counters (asynchronous). */
+/* Zero the table and all counters (asynchronous; Sec. 4.7 interface: the
+ * paper's filter is rebuilt by the caller after an insert failure, Alg. 1). */
 cf_status cf_clear(cf_filter* f, void* stream);
 
 /* Same three operations on HOST buffers: keys are streamed to the device in
- * chunks through library-owned staging buffers, flags are streamed back.
+ * chunks through library-owned staging buffers (four slots of keys, so
+ * that copies of later chunks overlap the kernels of earlier ones); flags
+ * are gathered on the device and copied back in pieces of about 256 MiB
+ * (two alternating device buffers).
  * Synchronous (returns when out_flags_host is filled).  Host buffers should
  * be pinned (cudaHostRegister / torch pin_memory) for overlap. */
 cf_status cf_insert_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
@@ -168,7 +185,25 @@ cf_status cf_contains_host(cf_filter* f, const uint64_t* keys_host,
                            uint64_t n, uint8_t* out_flags_host, void* stream);
 cf_status cf_remove_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
                          uint8_t* out_flags_host, void* stream);
-/* Keys per staging chunk for the *_host calls (default 2^24). */
+/* The same three calls, asynchronous: they enqueue the copies and kernels
+ * and return.  The flags are in out_flags_host once `stream` has
+ * synchronised (the stream waits for the last flag copy); keys_host must
+ * stay valid, and out_flags_host untouched, until then.  Consecutive calls
+ * on a filter overlap on the device (the next call's key copies run while
+ * the previous call's kernels run); they still execute in call order.
+ * When a call takes the slice-partitioned path (cf_set_slicing), each pass
+ * of up to the pass size gathers its keys staging chunk by staging chunk,
+ * so the pass size, not the staging chunk, sets how often the table is
+ * swept. */
+cf_status cf_insert_host_async(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                               uint8_t* out_flags_host, void* stream);
+cf_status cf_contains_host_async(cf_filter* f, const uint64_t* keys_host,
+                                 uint64_t n, uint8_t* out_flags_host, void* stream);
+cf_status cf_remove_host_async(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                               uint8_t* out_flags_host, void* stream);
+/* Keys per staging chunk for the *_host calls (default 2^24; the library
+ * keeps eight chunks of keys and two flag buffers of at least 256 MiB or a
+ * sliced pass).  Waits for the filter's queued work. */
 cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk);
 
 /* Slice-partitioned execution of cf_insert / cf_contains / cf_remove (and of
@@ -200,13 +235,39 @@ cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk);
 cf_status cf_set_slicing(cf_filter* f, int mode, uint64_t slice_bytes,
                          uint64_t max_chunk);
 
+/* Full-bucket map of the insert's eviction loop.  The BFS heuristic of
+ * Sec. 4.6.1 asks, for each of b/2 candidates, whether the candidate's
+ * alternate bucket has an empty slot.  On a table L2 cannot hold, asking the
+ * bucket is a random DRAM access per candidate.  With the map, one bit per
+ * bucket (m/8 bytes, allocated by the library on first use, freed by
+ * cf_destroy) answers instead: it is built from the table by one pass
+ * before the eviction kernel, and the eviction rounds set the bit of every
+ * bucket they fill or find full.  During an insert a full bucket stays full,
+ * so a set bit is always right; a clear bit that has gone stale costs one
+ * failed insert attempt, after which the chain goes on from that bucket as
+ * it would had a concurrent insert taken the room.  Every key still follows
+ * Alg. 1 and Sec. 4.6.1, and a single thread (cf_debug_insert_serial) takes
+ * exactly the same steps with or without the map.
+ *  - mode: 0 never; 1 automatic (the default): BFS filters whose table is
+ *    larger than 64 MiB; 2 always (BFS filters).
+ *  - min_queue: the map is built and used only for eviction queues of at
+ *    least this many keys (0: m/16 in automatic mode, every queue in mode
+ *    2); smaller queues probe the buckets.
+ *  - cf_debug_insert_serial uses (and keeps exact) the map in mode 2.
+ * CF_EINVAL for a bad mode.  Takes effect with the next insert call. */
+cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue);
+
 /* ---- state, stats, snapshots (synchronous) ------------------------------ */
+/* Counters of the filter (Sec. 4.3: the occupancy count kept by the
+ * insert's hierarchical reduction; Sec. 4.7 interface).  Syncs `stream`. */
 cf_status cf_stats(cf_filter* f, cf_stats_t* out, void* stream);
 /* Copy the first min(max, logged) victims (tag, bucket) to host arrays;
  * *count receives the number logged (capped at the capacity). */
 cf_status cf_victims(cf_filter* f, uint32_t* tags_host, uint64_t* buckets_host,
                      uint64_t max, uint64_t* count, void* stream);
-/* Snapshot = 64-byte little-endian header (magic "CFG1", version 1, m, f,
+/* Snapshot and restore of the table of Sec. 4.2 (Sec. 4.7 interface; the
+ * paper has no file format, this one is the library's own).
+ * Snapshot = 64-byte little-endian header (magic "CFG1", version 1, m, f,
  * b, max_evictions, policy, occupancy, table bytes, hash id 1, eviction)
  * followed by the raw table.  dst/src may be host (is_device = 0) or
  * device (is_device = 1) memory of at least cf_snapshot_bytes bytes.
@@ -232,6 +293,13 @@ cf_status cf_hash_debug(const uint64_t* keys, uint64_t n, uint32_t fp_bits,
 cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
                                  uint64_t n, uint8_t* out_flags,
                                  uint32_t* evictions_out, void* stream);
+/* Bound of every CAS retry loop of the filter's kernels (attempts on one
+ * word before the key is given up with CF_FLAG_CONTENTION): 1 .. 4096, 0
+ * restores the default 4096; CF_EINVAL above 4096.  Lowering it makes the
+ * bounded loops run out under ordinary contention, so that tests can reach
+ * the contention path (flags, counter, victim, error-word bit 0) without
+ * any kernel waiting unboundedly.  Applies to calls made after it. */
+cf_status cf_debug_set_cas_limit(cf_filter* f, uint32_t limit);
 
 /* ---- multi-filter launch --------------------------------------------------
  * Many filters' insert / query / delete batches in ONE persistent kernel
@@ -401,18 +469,25 @@ cf_status cf_plain_run_trace(cf_filter* const* filters, uint32_t n_filters,
  * memory is all handed out by another allocator or a fixed-size arena,
  * code on a path that must not stall on cudaMalloc's implicit device
  * synchronisation, and code that must not fail with out-of-memory halfway
- * through a batch.  cf_insert_noalloc does exactly the insert of cf_insert
- * (same kernels, same results and flags) with its queue in a fixed array
- * compiled into the library: a file-scope __device__ array of
- * CF_NOALLOC_MAX_KEYS entries (4 MiB), which every GPU that loads the
- * library holds until the process exits.  It calls no cudaMalloc, cudaFree
- * or other device-allocating routine.  Keys and flags are still the
- * caller's; build the filter with cf_create_at to keep the whole path free
- * of library allocations.
+ * through a batch.  cf_insert_noalloc runs the plain two-kernel insert
+ * (direct insertion into i1 / i2, then the eviction loop of Sec. 4.6.1 over
+ * the queued keys) with its queue in a fixed array compiled into the
+ * library: a file-scope __device__ array of CF_NOALLOC_MAX_KEYS entries
+ * (4 MiB), which every GPU that loads the library holds until the process
+ * exits.  It ignores the filter's slicing mode (cf_set_slicing): it never
+ * takes the slice-partitioned path, which needs scratch memory.  Its
+ * results obey the same rules as cf_insert's (flags, counters, victims,
+ * the multiset of stored tags); where several placements are valid, the
+ * two entry points may pick different ones.  It calls no cudaMalloc,
+ * cudaFree or other device-allocating routine.  Keys and flags are still
+ * the caller's; build the filter with cf_create_at to keep the whole path
+ * free of library allocations.
  *  - n > CF_NOALLOC_MAX_KEYS returns CF_EINVAL (split larger batches).
  *  - The filter's device must be the current device (CF_EINVAL otherwise).
- *    The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *    Every call looks up the array's device address in the current context
+ *    with cudaGetSymbolAddress (CF_ECUDA if that fails).  The first call on
+ *    a device also loads the library's device code there; make that first
+ *    call before any stream capture.
  *  - Every call shares the one array: calls whose GPU work overlaps (on
  *    streams not ordered with each other, on any filters) race and corrupt
  *    each other's results.  Issue them on one stream or order the streams.
@@ -430,10 +505,11 @@ cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
  * insert phase 1 (direct insertion into i1 / i2), 1: insert phase 2
  * (eviction loop, both paths), 2: contains, 3: remove; slice-partitioned
  * path (cf_set_slicing): 4: grouping by slice (counter reset, scatter),
- * 5: bucket-i1 pass, 6: bucket-i2 pass, 7: results back to key order.
+ * 5: bucket-i1 pass, 6: bucket-i2 pass, 7: results back to key order;
+ * 8: the full-bucket map of the eviction loop (cf_set_eviction_map).
  * cf_read_kernel_times waits for the recorded events, sums their elapsed
  * times and (reset != 0) recycles them. */
-#define CF_KERNEL_KINDS 8
+#define CF_KERNEL_KINDS 9
 typedef struct {
   uint64_t launches[CF_KERNEL_KINDS];
   double ms[CF_KERNEL_KINDS];
@@ -451,16 +527,6 @@ cf_status cf_probe_gather(const void* buf, uint64_t bytes, uint64_t n_access,
                           uint32_t access_bytes, uint32_t loads_per_thread,
                           uint64_t seed, unsigned long long* sink,
                           void* stream);
-/* The same random 8-byte loads with a chosen load form: flavour 0
- * ld.global.nc.L1::no_allocate, 1 ld.global.cg, 2 ld.global.cs, 3
- * ld.global (default), 4 ld.global.lu, 5 ld.relaxed.gpu.global, 6
- * ld.volatile.global, 7 flavour 0 with the .L2::64B prefetch-size hint, 8
- * with .L2::256B, 9 atom.global.or.b64 with 0 (a read performed at L2);
- * 8 loads in flight per thread.  The buffer is not modified. */
-cf_status cf_probe_gather_flavour(const void* buf, uint64_t bytes,
-                                  uint64_t n_access, uint32_t flavour,
-                                  uint64_t seed, unsigned long long* sink,
-                                  void* stream);
 /* The CUDA context limit cudaLimitMaxL2FetchGranularity of the current
  * device (0..128 bytes): how much L2 fetches from DRAM around a missed
  * sector.  Random bucket probes use one 32-byte sector; a larger fetch

@@ -24,7 +24,8 @@ class CfStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "occupancy", "insert_ok", "insert_fail", "remove_ok", "remove_fail",
         "evictions", "victims", "rollbacks", "rollback_lost", "contention")] + [
-        ("error_word", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32)]
+        ("error_word", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32),
+        ("map_builds", ctypes.c_uint64), ("cas_retry", ctypes.c_uint64 * 7)]
 
 
 class CfBatchItem(ctypes.Structure):
@@ -65,7 +66,8 @@ class CfServerStats(ctypes.Structure):
 
 
 KERNEL_KINDS = ("insert_direct", "insert_evict", "contains", "remove",
-                "slice_split", "slice_probe1", "slice_probe2", "slice_merge")
+                "slice_split", "slice_probe1", "slice_probe2", "slice_merge",
+                "evict_map")
 
 
 class CfKernelTimes(ctypes.Structure):
@@ -78,7 +80,7 @@ _vp, _u64, _u32, _int = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctype
 _st = ctypes.c_int
 _pcfg = ctypes.POINTER(CfConfig)
 SIGNATURES = {
-    "cf_table_bytes": (ctypes.c_size_t, [_pcfg]),
+    "cf_table_bytes": (ctypes.c_size_t, [_u64, _u32, _u32]),
     "cf_required_bytes": (ctypes.c_size_t, [_pcfg]),
     "cf_snapshot_bytes": (ctypes.c_size_t, [_vp]),
     "cf_create": (_st, [_u64, _u32, _u32, _u32, ctypes.POINTER(_vp)]),
@@ -95,8 +97,13 @@ SIGNATURES = {
     "cf_insert_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
     "cf_contains_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
     "cf_remove_host": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_insert_host_async": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_contains_host_async": (_st, [_vp, _vp, _u64, _vp, _vp]),
+    "cf_remove_host_async": (_st, [_vp, _vp, _u64, _vp, _vp]),
     "cf_set_staging_chunk": (_st, [_vp, _u64]),
     "cf_set_slicing": (_st, [_vp, _int, _u64, _u64]),
+    "cf_set_eviction_map": (_st, [_vp, _int, _u64]),
+    "cf_debug_set_cas_limit": (_st, [_vp, _u32]),
     "cf_stats": (_st, [_vp, ctypes.POINTER(CfStats), _vp]),
     "cf_victims": (_st, [_vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "cf_snapshot": (_st, [_vp, _vp, ctypes.c_size_t, _int, _vp]),
@@ -132,7 +139,6 @@ SIGNATURES = {
     "cf_set_kernel_timing": (_st, [_vp, _int]),
     "cf_read_kernel_times": (_st, [_vp, ctypes.POINTER(CfKernelTimes), _int]),
     "cf_probe_gather": (_st, [_vp, _u64, _u64, _u32, _u32, _u64, _vp, _vp]),
-    "cf_probe_gather_flavour": (_st, [_vp, _u64, _u64, _u32, _u64, _vp, _vp]),
     "cf_set_l2_fetch_granularity": (_st, [_u32]),
     "cf_get_l2_fetch_granularity": (_st, [ctypes.POINTER(_u32)]),
     "cf_status_str": (ctypes.c_char_p, [_st]),

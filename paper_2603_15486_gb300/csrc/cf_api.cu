@@ -4,8 +4,9 @@
 //   [control block 256 B][victim log, 16 B per entry][table]
 // (each piece 256-byte aligned), plus library-owned scratch: the eviction
 // work queue of the insert (4 bytes per key of the largest chunk seen), the
-// scratch of the slice-partitioned path (about 48 bytes per key of its chunk)
-// and, for the *_host calls, two staging slots of keys and flags.
+// scratch of the slice-partitioned path (about 48 bytes per key of its chunk),
+// the full-bucket map of the eviction loop (m/8 bytes) and, for the *_host
+// calls, four staging slots of keys and two device buffers of flags.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -102,6 +103,7 @@ DevFilter make_dev(const cf_config* c, char* mem) {
   d.fm_m1 = fastmod_magic(c->num_buckets - 1);
   d.max_ev = c->max_evictions;
   d.eviction = c->eviction;
+  d.max_cas = cfk::kMaxCas;
   return d;
 }
 
@@ -226,35 +228,62 @@ cf_status init_filter(cf_filter* f, const cf_config* cfg, char* mem,
 void free_staging(cf_filter* f) {
   for (auto& st : f->stage) {
     if (st.keys) cudaFree(st.keys);
-    if (st.flags) cudaFree(st.flags);
     if (st.in_done) cudaEventDestroy(st.in_done);
     if (st.comp_done) cudaEventDestroy(st.comp_done);
-    if (st.out_done) cudaEventDestroy(st.out_done);
     st = Stage{};
+  }
+  for (auto& g : f->fgroup) {
+    if (g.flags) cudaFree(g.flags);
+    if (g.comp_done) cudaEventDestroy(g.comp_done);
+    if (g.out_done) cudaEventDestroy(g.out_done);
+    g = cfk::FlagGroup{};
   }
   if (f->s_in) cudaStreamDestroy(f->s_in);
   if (f->s_out) cudaStreamDestroy(f->s_out);
   f->s_in = f->s_out = nullptr;
+  f->next_slot = f->next_group = 0;
   f->stage_ready = false;
 }
 
 cf_status ensure_staging(cf_filter* f) {
   if (f->stage_ready) return CF_OK;
   const uint64_t c = f->stage_chunk;
+  f->group_chunks = cfk::kFlagGroupBytes / c ? cfk::kFlagGroupBytes / c : 1;
   for (auto& st : f->stage) {
-    if (cudaMalloc(&st.keys, c * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&st.flags, c) != cudaSuccess) {
+    if (cudaMalloc(&st.keys, c * sizeof(uint64_t)) != cudaSuccess) {
       cudaGetLastError();
       free_staging(f);
       return CF_ENOMEM;
     }
     CF_CUDA(cudaEventCreateWithFlags(&st.in_done, cudaEventDisableTiming));
     CF_CUDA(cudaEventCreateWithFlags(&st.comp_done, cudaEventDisableTiming));
-    CF_CUDA(cudaEventCreateWithFlags(&st.out_done, cudaEventDisableTiming));
+  }
+  for (auto& g : f->fgroup) {
+    CF_CUDA(cudaEventCreateWithFlags(&g.comp_done, cudaEventDisableTiming));
+    CF_CUDA(cudaEventCreateWithFlags(&g.out_done, cudaEventDisableTiming));
   }
   CF_CUDA(cudaStreamCreateWithFlags(&f->s_in, cudaStreamNonBlocking));
   CF_CUDA(cudaStreamCreateWithFlags(&f->s_out, cudaStreamNonBlocking));
   f->stage_ready = true;
+  return CF_OK;
+}
+
+// Both flag buffers hold at least `bytes`.  Growing one waits for the work
+// that still uses it.
+cf_status ensure_flag_groups(cf_filter* f, uint64_t bytes) {
+  for (auto& g : f->fgroup) {
+    if (g.cap >= bytes) continue;
+    if (g.used) CF_CUDA(cudaEventSynchronize(g.out_done));
+    if (g.flags) CF_CUDA(cudaFree(g.flags));
+    g.flags = nullptr;
+    g.cap = 0;
+    if (cudaMalloc(&g.flags, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(g_err, sizeof g_err, "flag staging of %llu bytes", (unsigned long long)bytes);
+      return CF_ENOMEM;
+    }
+    g.cap = bytes;
+  }
   return CF_OK;
 }
 
@@ -281,6 +310,49 @@ bool use_sliced(const cf_filter* f, uint64_t n, const uint32_t* evout) {
   if (evout || f->slice_mode == 0) return false;
   if (f->slice_mode == 2) return true;
   return table_bytes(&f->cfg) >= kSliceAutoTable && n >= f->cfg.num_buckets / 8;
+}
+
+// Full-bucket map of the eviction loop (bfs_round_map).  Automatic rule:
+// BFS filters whose table L2 does not hold (more than 64 MiB), for eviction
+// queues of at least m/16 keys.  Building the map reads the whole table
+// once (about 0.33 ms for 2 GiB); each BFS round then loads one bucket
+// instead of one per inspected candidate, which pays once the queue holds a
+// few million chains.  Below the threshold the map kernel returns at once
+// and the eviction loop probes buckets as before.
+uint32_t map_min_queue(const cf_filter* f) {
+  if (f->map_min_queue) return uint32_t(f->map_min_queue < 0xFFFFFFFFull ? f->map_min_queue : 0xFFFFFFFFull);
+  if (f->map_mode == 2) return 0;
+  const uint64_t q = f->cfg.num_buckets / 16;
+  return uint32_t(q < 0xFFFFFFFFull ? (q ? q : 1) : 0xFFFFFFFFull);
+}
+
+bool use_map(const cf_filter* f) {
+  if (f->map_mode == 0 || f->cfg.eviction != CF_EVICT_BFS) return false;
+  if (f->map_mode == 2) return true;
+  return table_bytes(&f->cfg) > cfk::kL2TableBytes;
+}
+
+cf_status ensure_map(cf_filter* f) {
+  if (f->fullmap) return CF_OK;
+  const size_t words = size_t((f->cfg.num_buckets + 31) / 32);
+  if (cudaMalloc(&f->fullmap, words * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    f->fullmap = nullptr;
+    snprintf(g_err, sizeof g_err, "full-bucket map of %zu bytes", words * 4);
+    return CF_ENOMEM;
+  }
+  return CF_OK;
+}
+
+// The map argument of one insert call (allocating the map on first use).
+cf_status evict_map_for(cf_filter* f, cfk::EvictMap* em) {
+  *em = cfk::EvictMap{};
+  if (!use_map(f)) return CF_OK;
+  cf_status st = ensure_map(f);
+  if (st != CF_OK) return st;
+  em->bits = f->fullmap;
+  em->min_q = map_min_queue(f);
+  return CF_OK;
 }
 
 void free_slice(cf_filter* f) {
@@ -353,15 +425,18 @@ cf_status run_sliced(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
   const uint64_t chunk = (n + passes - 1) / passes;
   cf_status st = ensure_slice(f, chunk);
   if (st != CF_OK) return st;
+  cfk::EvictMap em;
   if (op == OP_INSERT) {
     st = ensure_queue(f, chunk, kSliceChunkMax);
+    if (st != CF_OK) return st;
+    st = evict_map_for(f, &em);
     if (st != CF_OK) return st;
   }
   for (uint64_t off = 0; off < n; off += chunk) {
     const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
     const cudaError_t e = f->ops->sliced(f->d, int(op), keys + off, len,
                                          flags ? flags + off : nullptr, f->sb,
-                                         f->queue, s, f->timer);
+                                         f->queue, em, s, f->timer);
     if (e != cudaSuccess) {
       set_err("sliced kernel launch", e);
       return CF_ECUDA;
@@ -381,11 +456,14 @@ cf_status run_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
   } else {
     cf_status st = ensure_queue(f, n);
     if (st != CF_OK) return st;
+    cfk::EvictMap em;
+    st = evict_map_for(f, &em);
+    if (st != CF_OK) return st;
     for (uint64_t off = 0; off < n && e == cudaSuccess; off += kInsertChunk) {
       const uint64_t len = (n - off) < kInsertChunk ? (n - off) : kInsertChunk;
       e = f->ops->insert_chunk(f->d, keys + off, uint32_t(len),
                                flags ? flags + off : nullptr,
-                               evout ? evout + off : nullptr, f->queue, s,
+                               evout ? evout + off : nullptr, f->queue, em, s,
                                f->timer);
     }
   }
@@ -409,46 +487,161 @@ cf_status device_op(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
   return mark(f, s);
 }
 
-// Host-buffer form: kStageSlots staging slots; the H2D copies of the next
-// chunks (stream s_in) overlap the kernels of chunk c (the caller's stream)
-// and the D2H of earlier chunks' flags (stream s_out).
+// Host-buffer forms.  Keys go through the kStageSlots staging slots in turn
+// (stream s_in); a slot is reused once the kernels that read its previous
+// chunk are done.  Flags are written to one of two device flag buffers
+// (used in turn) and copied back in one piece per buffer fill (stream
+// s_out); a buffer is reused once its previous copy is done.  Slots and
+// buffers rotate across calls, so consecutive asynchronous calls overlap:
+// the next call's key copies run while this call's kernels run.  At the
+// end the caller's stream waits for the last flag copy, so the caller's
+// stream completing means the flags are in host memory.
+
+// One staging chunk of keys onto the device; returns its slot (the caller's
+// stream waits for the copy).
+cf_status stage_keys(cf_filter* f, const uint64_t* keys_h, uint64_t len, cudaStream_t s,
+                     Stage** out) {
+  Stage& sg = f->stage[f->next_slot];
+  f->next_slot = (f->next_slot + 1) % cfk::kStageSlots;
+  if (sg.used) CF_CUDA(cudaStreamWaitEvent(f->s_in, sg.comp_done, 0));
+  CF_CUDA(cudaMemcpyAsync(sg.keys, keys_h, len * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                          f->s_in));
+  CF_CUDA(cudaEventRecord(sg.in_done, f->s_in));
+  CF_CUDA(cudaStreamWaitEvent(s, sg.in_done, 0));
+  *out = &sg;
+  return CF_OK;
+}
+
+// The next flag buffer, once its previous copy to the host is done.
+cfk::FlagGroup* take_group(cf_filter* f, cudaStream_t s) {
+  cfk::FlagGroup* g = &f->fgroup[f->next_group];
+  f->next_group ^= 1u;
+  if (g->used) cudaStreamWaitEvent(s, g->out_done, 0);
+  return g;
+}
+
+// Copy `bytes` of flags from a buffer to the host after the kernels so far.
+cf_status flush_group(cf_filter* f, cfk::FlagGroup* g, uint8_t* dst_h, uint64_t bytes,
+                      cudaStream_t s, cudaEvent_t* last_out) {
+  CF_CUDA(cudaEventRecord(g->comp_done, s));
+  CF_CUDA(cudaStreamWaitEvent(f->s_out, g->comp_done, 0));
+  CF_CUDA(cudaMemcpyAsync(dst_h, g->flags, bytes, cudaMemcpyDeviceToHost, f->s_out));
+  CF_CUDA(cudaEventRecord(g->out_done, f->s_out));
+  g->used = true;
+  *last_out = g->out_done;
+  return CF_OK;
+}
+
+// Sliced path: passes of up to the filter's pass size; each pass's keys
+// arrive in staging chunks, each scattered as it lands, then the pass's
+// bucket passes, eviction loop and result passes run once, and the pass's
+// flags go back in one copy.
+cf_status host_sliced(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
+                      uint8_t* flags_h, cudaStream_t s, cudaEvent_t* last_out) {
+  const uint64_t cap = slice_chunk(f);
+  const uint64_t passes = (n + cap - 1) / cap;
+  const uint64_t plen = (n + passes - 1) / passes;
+  cf_status st = ensure_slice(f, plen);
+  if (st != CF_OK) return st;
+  cfk::EvictMap em;
+  if (op == OP_INSERT) {
+    st = ensure_queue(f, plen, kSliceChunkMax);
+    if (st != CF_OK) return st;
+    st = evict_map_for(f, &em);
+    if (st != CF_OK) return st;
+  }
+  if (flags_h) {
+    st = ensure_flag_groups(f, plen);
+    if (st != CF_OK) return st;
+  }
+  const uint64_t chunk = f->stage_chunk;
+  for (uint64_t p0 = 0; p0 < n; p0 += plen) {
+    const uint64_t pl = (n - p0) < plen ? (n - p0) : plen;
+    cudaError_t e = f->ops->sliced_begin(f->sb, s);
+    for (uint64_t c0 = 0; c0 < pl && e == cudaSuccess; c0 += chunk) {
+      const uint64_t len = (pl - c0) < chunk ? (pl - c0) : chunk;
+      Stage* sg = nullptr;
+      st = stage_keys(f, keys_h + p0 + c0, len, s, &sg);
+      if (st != CF_OK) return st;
+      e = f->ops->sliced_scatter(f->d, sg->keys, len, c0, flags_h != nullptr, f->sb, s,
+                                 f->timer);
+      if (e == cudaSuccess) e = cudaEventRecord(sg->comp_done, s);
+      sg->used = true;
+    }
+    cfk::FlagGroup* g = flags_h ? take_group(f, s) : nullptr;
+    if (e == cudaSuccess)
+      e = f->ops->sliced_finish(f->d, int(op), pl, g ? g->flags : nullptr, f->sb, f->queue,
+                                em, s, f->timer);
+    if (e != cudaSuccess) {
+      set_err("sliced kernel launch", e);
+      return CF_ECUDA;
+    }
+    if (g) {
+      st = flush_group(f, g, flags_h + p0, pl, s, last_out);
+      if (st != CF_OK) return st;
+    }
+  }
+  return CF_OK;
+}
+
+// Plain path: every staging chunk runs the single-filter kernels; the flags
+// of group_chunks consecutive chunks share one buffer and one copy back.
+cf_status host_chunked(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
+                       uint8_t* flags_h, cudaStream_t s, cudaEvent_t* last_out) {
+  const uint64_t chunk = f->stage_chunk;
+  const uint64_t G = f->group_chunks;
+  if (op == OP_INSERT) {
+    cf_status st = ensure_queue(f, chunk);
+    if (st != CF_OK) return st;
+  }
+  if (flags_h) {
+    cf_status st = ensure_flag_groups(f, G * chunk);
+    if (st != CF_OK) return st;
+  }
+  const uint64_t nchunks = (n + chunk - 1) / chunk;
+  cfk::FlagGroup* g = nullptr;
+  uint64_t g0 = 0;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    const uint64_t off = c * chunk;
+    const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
+    Stage* sg = nullptr;
+    cf_status st = stage_keys(f, keys_h + off, len, s, &sg);
+    if (st != CF_OK) return st;
+    if (flags_h && c % G == 0) {
+      g = take_group(f, s);
+      g0 = off;
+    }
+    st = run_op(f, op, sg->keys, len, g ? g->flags + (off - g0) : nullptr, nullptr, s);
+    if (st != CF_OK) return st;
+    CF_CUDA(cudaEventRecord(sg->comp_done, s));
+    sg->used = true;
+    if (g && (c % G == G - 1 || c == nchunks - 1)) {
+      st = flush_group(f, g, flags_h + g0, off + len - g0, s, last_out);
+      if (st != CF_OK) return st;
+      g = nullptr;
+    }
+  }
+  return CF_OK;
+}
+
 cf_status host_op(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
-                  uint8_t* flags_h, void* stream) {
+                  uint8_t* flags_h, void* stream, bool wait) {
   if (!f) return CF_EINVAL;
   if (n == 0) return CF_OK;
   if (!keys_h) return CF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cf_status st = ensure_staging(f);
   if (st != CF_OK) return st;
-  if (op == OP_INSERT) {
-    st = ensure_queue(f, f->stage_chunk);
-    if (st != CF_OK) return st;
-  }
   st = order_on(f, s);
   if (st != CF_OK) return st;
-  const uint64_t chunk = f->stage_chunk;
-  const uint64_t nchunks = (n + chunk - 1) / chunk;
-  for (uint64_t c = 0; c < nchunks; ++c) {
-    Stage& sg = f->stage[c % cfk::kStageSlots];
-    const uint64_t off = c * chunk;
-    const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
-    if (c >= cfk::kStageSlots) CF_CUDA(cudaStreamWaitEvent(f->s_in, sg.out_done, 0));
-    CF_CUDA(cudaMemcpyAsync(sg.keys, keys_h + off, len * sizeof(uint64_t),
-                            cudaMemcpyHostToDevice, f->s_in));
-    CF_CUDA(cudaEventRecord(sg.in_done, f->s_in));
-    CF_CUDA(cudaStreamWaitEvent(s, sg.in_done, 0));
-    st = run_op(f, op, sg.keys, len, sg.flags, nullptr, s);
-    if (st != CF_OK) return st;
-    CF_CUDA(cudaEventRecord(sg.comp_done, s));
-    CF_CUDA(cudaStreamWaitEvent(f->s_out, sg.comp_done, 0));
-    if (flags_h)
-      CF_CUDA(cudaMemcpyAsync(flags_h + off, sg.flags, len,
-                              cudaMemcpyDeviceToHost, f->s_out));
-    CF_CUDA(cudaEventRecord(sg.out_done, f->s_out));
-  }
+  cudaEvent_t last_out = nullptr;
+  st = use_sliced(f, n, nullptr) ? host_sliced(f, op, keys_h, n, flags_h, s, &last_out)
+                                 : host_chunked(f, op, keys_h, n, flags_h, s, &last_out);
+  if (st != CF_OK) return st;
+  if (last_out) CF_CUDA(cudaStreamWaitEvent(s, last_out, 0));
   st = mark(f, s);
   if (st != CF_OK) return st;
-  CF_CUDA(cudaStreamSynchronize(f->s_out));
+  if (wait) CF_CUDA(cudaStreamSynchronize(s));
   return CF_OK;
 }
 
@@ -515,7 +708,20 @@ cf_status cf_set_slicing(cf_filter* f, int mode, uint64_t slice_bytes,
   return CF_OK;
 }
 
-int cf_version(void) { return 10000; }
+cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue) {
+  if (!f || mode < 0 || mode > 2) return CF_EINVAL;
+  f->map_mode = mode;
+  f->map_min_queue = min_queue;
+  return CF_OK;
+}
+
+cf_status cf_debug_set_cas_limit(cf_filter* f, uint32_t limit) {
+  if (!f || limit > cfk::kMaxCas) return CF_EINVAL;
+  f->d.max_cas = limit ? limit : cfk::kMaxCas;
+  return CF_OK;
+}
+
+int cf_version(void) { return 10100; }
 
 const char* cf_status_str(cf_status s) {
   switch (s) {
@@ -531,8 +737,11 @@ const char* cf_status_str(cf_status s) {
   return "unknown status";
 }
 
-size_t cf_table_bytes(const cf_config* cfg) {
-  return valid_config(cfg) ? table_bytes(cfg) : 0;
+size_t cf_table_bytes(uint64_t num_buckets, uint32_t fp_bits, uint32_t slots_per_bucket) {
+  if (!(fp_bits == 8 || fp_bits == 16 || fp_bits == 32)) return 0;
+  if (!(slots_per_bucket == 4 || slots_per_bucket == 8 || slots_per_bucket == 16)) return 0;
+  if (num_buckets == 0 || num_buckets > (1ull << 32)) return 0;
+  return size_t(num_buckets) * slots_per_bucket * fp_bits / 8;
 }
 
 size_t cf_required_bytes(const cf_config* cfg) {
@@ -600,6 +809,7 @@ cf_status cf_destroy(cf_filter* f) {
   if (f->has_last) cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev);
   free_staging(f);
   if (f->queue) cudaFree(f->queue);
+  if (f->fullmap) cudaFree(f->fullmap);
   free_slice(f);
   if (f->last_ev) cudaEventDestroy(f->last_ev);
   delete f->timer;
@@ -640,18 +850,34 @@ cf_status cf_remove(cf_filter* f, const uint64_t* keys, uint64_t n,
 
 cf_status cf_insert_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
                          uint8_t* out_flags_host, void* stream) {
-  return host_op(f, OP_INSERT, keys_host, n, out_flags_host, stream);
+  return host_op(f, OP_INSERT, keys_host, n, out_flags_host, stream, true);
 }
 
 cf_status cf_contains_host(cf_filter* f, const uint64_t* keys_host,
                            uint64_t n, uint8_t* out_flags_host, void* stream) {
   if (f && n && !out_flags_host) return CF_EINVAL;
-  return host_op(f, OP_CONTAINS, keys_host, n, out_flags_host, stream);
+  return host_op(f, OP_CONTAINS, keys_host, n, out_flags_host, stream, true);
 }
 
 cf_status cf_remove_host(cf_filter* f, const uint64_t* keys_host, uint64_t n,
                          uint8_t* out_flags_host, void* stream) {
-  return host_op(f, OP_REMOVE, keys_host, n, out_flags_host, stream);
+  return host_op(f, OP_REMOVE, keys_host, n, out_flags_host, stream, true);
+}
+
+cf_status cf_insert_host_async(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                               uint8_t* out_flags_host, void* stream) {
+  return host_op(f, OP_INSERT, keys_host, n, out_flags_host, stream, false);
+}
+
+cf_status cf_contains_host_async(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                                 uint8_t* out_flags_host, void* stream) {
+  if (f && n && !out_flags_host) return CF_EINVAL;
+  return host_op(f, OP_CONTAINS, keys_host, n, out_flags_host, stream, false);
+}
+
+cf_status cf_remove_host_async(cf_filter* f, const uint64_t* keys_host, uint64_t n,
+                               uint8_t* out_flags_host, void* stream) {
+  return host_op(f, OP_REMOVE, keys_host, n, out_flags_host, stream, false);
 }
 
 cf_status cf_set_staging_chunk(cf_filter* f, uint64_t keys_per_chunk) {
@@ -693,6 +919,8 @@ cf_status cf_stats(cf_filter* f, cf_stats_t* out, void* stream) {
   out->contention = c.contention;
   out->error_word = c.error_word;
   out->victim_capacity = f->d.victim_cap;
+  out->map_builds = c.map_builds;
+  for (int i = 0; i < 7; ++i) out->cas_retry[i] = c.cas_retry[i];
   return mark(f, s);
 }
 
@@ -832,7 +1060,16 @@ cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cf_status st = order_on(f, s);
   if (st != CF_OK) return st;
-  cudaError_t e = f->ops->insert_serial(f->d, keys, n, out_flags, evictions_out, s);
+  // The serial kernel uses the full-bucket map when the filter's map mode
+  // is "always" (and keeps it exact), so that the map-based BFS round can
+  // be compared with the sequential oracle bit for bit.
+  uint32_t* map = nullptr;
+  if (f->map_mode == 2 && f->cfg.eviction == CF_EVICT_BFS) {
+    st = ensure_map(f);
+    if (st != CF_OK) return st;
+    map = f->fullmap;
+  }
+  cudaError_t e = f->ops->insert_serial(f->d, keys, n, out_flags, evictions_out, map, s);
   if (e != cudaSuccess) {
     set_err("serial insert", e);
     return CF_ECUDA;

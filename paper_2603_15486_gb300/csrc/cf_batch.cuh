@@ -116,12 +116,14 @@ k_batch_tiles(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
       warp_add(&d.ctrl->insert_ok, c.ok, lane);
       warp_add(&d.ctrl->insert_fail, c.cont, lane);
       warp_add(&d.ctrl->contention, c.cont, lane);
+      warp_add(&d.ctrl->cas_retry[0], c.cas_first, lane);
     } else {
       tile_remove<G, K>(d, I.keys, I.n, base, lane, I.flags, c);
       warp_add(&d.ctrl->occupancy, c.ok, lane, /*negate=*/true);
       warp_add(&d.ctrl->remove_ok, c.ok, lane);
       warp_add(&d.ctrl->remove_fail, c.fail + c.cont, lane);
       warp_add(&d.ctrl->contention, c.cont, lane);
+      warp_add(&d.ctrl->cas_retry[0], c.cas_first, lane);
     }
   }
 }
@@ -178,6 +180,7 @@ k_batch_evict(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
         atomicAdd(&d.ctrl->contention, (unsigned long long)ec.contention);
         atomicOr(&d.ctrl->error_word, 1u);
       }
+      if (ec.cas_first) atomicAdd(&d.ctrl->cas_retry[0], (unsigned long long)ec.cas_first);
       if (r != ROUND_CONTINUE) {
         if (r != EV_OK) log_victim(d, vt, vb);
         if (I.flags) st_flag(I.flags + q.y, uint8_t(r));

@@ -18,8 +18,22 @@
 
 namespace cfk {
 
-// Bound of every CAS retry loop on one word.
-constexpr int kMaxCas = 1 << 12;
+// Default bound of every CAS retry loop on one word (DevFilter::max_cas;
+// tests lower it to make the loops run out).
+constexpr uint32_t kMaxCas = 1u << 12;
+
+// Build knobs of the CAS bookkeeping: CF_CAS_HIST=0 leaves the CAS-retry
+// histogram empty; CF_CONST_CAS=1 bounds the retry loops by kMaxCas at
+// compile time (ignoring DevFilter::max_cas).
+#ifndef CF_CAS_HIST
+#define CF_CAS_HIST 1
+#endif
+#ifndef CF_CONST_CAS
+#define CF_CONST_CAS 0
+#endif
+__device__ __forceinline__ uint32_t cas_bound(const DevFilter& d) {
+  return CF_CONST_CAS ? kMaxCas : d.max_cas;
+}
 
 // ---------------------------------------------------------------------------
 // Geometry: F-bit tags, B slots per bucket, bucket policy.
@@ -369,6 +383,22 @@ __device__ __forceinline__ uint64_t rng_next(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
+// A failed CAS at retry depth r (0: the loop's first attempt) goes into the
+// filter's CAS-retry histogram.  First attempts fail often where many keys
+// meet in few buckets (the slice-grouped passes), so they are counted in
+// the thread (`first`, added to the histogram once per block or warp by
+// the kernel); deeper retries are rare and go to the histogram directly.
+__device__ __forceinline__ void note_cas_fail(const DevFilter& d, uint32_t r,
+                                              uint32_t& first) {
+  if (!CF_CAS_HIST) return;
+  if (r == 0) {
+    ++first;
+    return;
+  }
+  const int bin = r == 1 ? 1 : r < 4 ? 2 : r < 8 ? 3 : r < 16 ? 4 : r < 64 ? 5 : 6;
+  atomicAdd(&d.ctrl->cas_retry[bin], 1ull);
+}
+
 // ---------------------------------------------------------------------------
 // Single-key bucket operations (used by the eviction loops, the serial
 // kernel and the rollback path).
@@ -388,7 +418,7 @@ __device__ __forceinline__ typename G::Word* bucket_ptr(const DevFilter& d,
 // observed, so the caller can keep using it without another load.
 template <class G>
 __device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
-                                 Bucket<G>& bk) {
+                                 Bucket<G>& bk, uint32_t& first) {
   using W = typename G::Word;
   W* base = bucket_ptr<G>(d, j);
   const int start = int((tag % G::B) / G::kTpw);
@@ -399,7 +429,7 @@ __device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
     for (int tries = 0;; ++tries) {
       const W z = zero_lanes<G>(cur);
       if (!z) break;
-      if (tries == kMaxCas) return TI_CONTENTION;
+      if (uint32_t(tries) >= cas_bound(d)) return TI_CONTENTION;
       const int lane = first_lane<G>(z);
       const W desired = cur | (W(tag) << (lane * G::F));
       const W old = atomicCAS(base + w, cur, desired);
@@ -407,6 +437,7 @@ __device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
         set_word<G>(bk, w, desired);
         return TI_OK;
       }
+      note_cas_fail(d, uint32_t(tries), first);
       cur = old;
     }
     set_word<G>(bk, w, cur);
@@ -415,14 +446,16 @@ __device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
 }
 
 template <class G>
-__device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag) {
+__device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag,
+                          uint32_t& first) {
   Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
-  return try_insert_loaded<G>(d, j, tag, bk);
+  return try_insert_loaded<G>(d, j, tag, bk, first);
 }
 
 // TryRemove (Alg. 3): same scan order; CAS the lowest matching lane to 0.
 template <class G>
-__device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag) {
+__device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag,
+                          uint32_t& first) {
   using W = typename G::Word;
   W* base = bucket_ptr<G>(d, j);
   const Bucket<G> bk = load_bucket<G, false>(base);
@@ -435,11 +468,12 @@ __device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag) {
     for (int tries = 0;; ++tries) {
       const W z = zero_lanes<G>(cur ^ pat);
       if (!z) break;
-      if (tries == kMaxCas) return TI_CONTENTION;
+      if (uint32_t(tries) >= cas_bound(d)) return TI_CONTENTION;
       const int lane = first_lane<G>(z);
       const W desired = cur & ~(G::kLaneMask << (lane * G::F));
       const W old = atomicCAS(base + w, cur, desired);
       if (old == cur) return TI_OK;
+      note_cas_fail(d, uint32_t(tries), first);
       cur = old;
     }
   }
@@ -448,6 +482,7 @@ __device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag) {
 
 struct EvictCounters {
   uint32_t rollbacks = 0, rollback_lost = 0, contention = 0;
+  uint32_t cas_first = 0;  // failed first CAS attempts (note_cas_fail)
 };
 
 // Result codes of the eviction loops (the key's flag).
@@ -503,7 +538,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   W* cbase = bucket_ptr<G>(d, c.cur);
   if (has_empty<G>(c.bk)) {
     // Only reachable under concurrency (a slot freed by a delete).
-    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk) == TI_OK) return EV_OK;
+    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first) == TI_OK) return EV_OK;
   }
   uint32_t t[H], mv[H];
   uint64_t a[H];
@@ -542,13 +577,14 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   W w = select_word<G>(c.bk, wi);
   bool swapped = false;
   uint32_t evicted = 0;
-  for (int tries = 0; tries < kMaxCas; ++tries) {
+  for (uint32_t tries = 0; tries < cas_bound(d); ++tries) {
     const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, c.tag));
     if (old == w) {
       evicted = get_lane<G>(w, lane);
       swapped = true;
       break;
     }
+    note_cas_fail(d, tries, ec.cas_first);
     w = old;
   }
   if (!swapped) {
@@ -567,7 +603,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
     c.bk = tb;  // the probe's words of that very bucket
   else
     c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
-  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk);
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
   if (r == TI_OK) return EV_OK;
   if (r == TI_CONTENTION) {
     ec.contention++;
@@ -592,13 +628,14 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   W w = select_word<G>(c.bk, wi);
   bool swapped = false;
   uint32_t evicted = 0;
-  for (int tries = 0; tries < kMaxCas; ++tries) {
+  for (uint32_t tries = 0; tries < cas_bound(d); ++tries) {
     const W old = atomicCAS(wp, w, replace_lane<G>(w, lane, c.tag));
     if (old == w) {
       evicted = get_lane<G>(w, lane);
       swapped = true;
       break;
     }
+    note_cas_fail(d, tries, ec.cas_first);
     w = old;
   }
   if (!swapped) {
@@ -613,7 +650,7 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   c.cur = alt_of<G>(d, c.cur, evicted, moved);
   c.tag = moved;
   c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
-  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk);
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
   if (r == TI_OK) return EV_OK;
   if (r == TI_CONTENTION) {
     ec.contention++;
@@ -621,6 +658,129 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
     vb = c.cur;
     return EV_CONTENTION;
   }
+  return ROUND_CONTINUE;
+}
+
+// ---------------------------------------------------------------------------
+// Full-bucket map of the eviction loop: bit j of the map is set only if
+// bucket j has no empty slot.  During an insert batch buckets only gain
+// tags, so a bucket once full stays full: a set bit is always right, and a
+// clear bit is either right or stale (the bucket has filled since).  The
+// map is built by one pass over the table before the eviction kernel and
+// kept up by the eviction rounds (a round that fills a bucket, or finds a
+// bucket full that the map called open, sets its bit).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t map_word(const uint32_t* map, uint64_t j) {
+  return ld_cg_u32(map + (j >> 5));  // L2: coherent with the atomicOr below
+}
+__device__ __forceinline__ void map_set(uint32_t* map, uint64_t j) {
+  atomicOr(map + (j >> 5), 1u << (j & 31));
+}
+
+// One round of the BFS eviction heuristic (Sec. 4.6.1) that asks the
+// full-bucket map, not the buckets themselves, whether each candidate's
+// alternate bucket has an empty slot.  Same candidates, same choice (the
+// first candidate, in order, whose alternate is open; else the last), same
+// swap-first move as bfs_round.  Only the bucket that receives the evicted
+// tag is loaded: it is the chosen candidate's alternate, which the next
+// step needs anyway (to insert into it, or as the next round's bucket), so
+// a round costs one bucket load from DRAM instead of one per inspected
+// candidate.  A stale clear bit costs what a stale loaded word costs under
+// concurrency: the insert finds the bucket full, the tag stays in hand and
+// the chain goes on from there (and the bit is set).  Run by one thread on
+// an exact map, the round takes the same steps as bfs_round.
+template <class G>
+__device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
+                             uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
+  using W = typename G::Word;
+  constexpr int H = G::B / 2;
+  const uint32_t start = uint32_t(rng_next(c.rng) & (G::B - 1));
+  W* cbase = bucket_ptr<G>(d, c.cur);
+  if (has_empty<G>(c.bk)) {
+    // Only reachable under concurrency (a slot freed by a delete).
+    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first) == TI_OK) {
+      if (!has_empty<G>(c.bk)) map_set(map, c.cur);
+      return EV_OK;
+    }
+  }
+  uint32_t t[H], mv[H], mw[H];
+  uint64_t a[H];
+  bool cand[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    t[k] = get_slot<G>(c.bk, (start + k) & (G::B - 1));
+    a[k] = alt_of<G>(d, c.cur, t[k], mv[k]);
+    cand[k] = t[k] != 0 && a[k] != c.cur;
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) mw[k] = cand[k] ? map_word(map, a[k]) : ~0u;
+  int chosen = H - 1;
+  bool open = false;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    if (!open && cand[k] && !((mw[k] >> (a[k] & 31)) & 1u)) {
+      open = true;
+      chosen = k;
+    }
+  }
+  // The words of the bucket the evicted tag goes to, loaded while the swap's
+  // CAS runs.
+  uint64_t an = 0;
+  bool pre = false;
+#pragma unroll
+  for (int k = 0; k < H; ++k)
+    if (k == chosen) {
+      an = a[k];
+      pre = cand[k];
+    }
+  Bucket<G> nb{};
+  if (pre) nb = load_bucket_ev<G>(bucket_ptr<G>(d, an));
+  const uint32_t sl = (start + uint32_t(chosen)) & (G::B - 1);
+  const int wi = int(sl / G::kTpw), lane = int(sl % G::kTpw);
+  W w = select_word<G>(c.bk, wi);
+  bool swapped = false;
+  uint32_t evicted = 0;
+  for (uint32_t tries = 0; tries < cas_bound(d); ++tries) {
+    const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, c.tag));
+    if (old == w) {
+      evicted = get_lane<G>(w, lane);
+      swapped = true;
+      break;
+    }
+    note_cas_fail(d, tries, ec.cas_first);
+    w = old;
+  }
+  if (!swapped) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  c.ev++;
+  if (evicted == 0) return EV_OK;
+  uint32_t moved;
+  const uint64_t dest = alt_of<G>(d, c.cur, evicted, moved);
+  uint32_t tk = 0;
+#pragma unroll
+  for (int k = 0; k < H; ++k)
+    if (k == chosen) tk = t[k];
+  c.bk = (pre && evicted == tk) ? nb : load_bucket_ev<G>(bucket_ptr<G>(d, dest));
+  c.cur = dest;
+  c.tag = moved;
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
+  if (r == TI_OK) {
+    if (!has_empty<G>(c.bk)) map_set(map, c.cur);
+    return EV_OK;
+  }
+  if (r == TI_CONTENTION) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  // c.cur is full.  Its bit is set already unless the map called it open
+  // (stale) or the move went elsewhere than the chosen candidate's bucket.
+  if (open || !pre || evicted != tk) map_set(map, c.cur);
   return ROUND_CONTINUE;
 }
 
@@ -689,6 +849,41 @@ __device__ int evict_key(const DevFilter& d, const KeyHash& kh, uint32_t& ev,
   int r;
   do {
     r = evict_round<G, FW>(d, c, vt, vb, ec);
+  } while (r == ROUND_CONTINUE);
+  ev = c.ev;
+  return r;
+}
+
+// evict_round with the full-bucket map for BFS (DFS never probes, so it
+// has no use for the map).
+template <class G>
+__device__ __forceinline__ int evict_round_map(const DevFilter& d, Chain<G>& c,
+                                               uint32_t* map, uint32_t& vt,
+                                               uint64_t& vb, EvictCounters& ec) {
+  if (c.ev >= d.max_ev) {
+    vt = c.tag;
+    vb = c.cur;
+    return EV_FAIL;
+  }
+  return d.eviction == 1 ? dfs_round<G>(d, c, vt, vb, ec)
+                         : bfs_round_map<G>(d, c, map, vt, vb, ec);
+}
+
+// evict_key with the full-bucket map (one thread; the serial kernel).
+template <class G>
+__device__ int evict_key_map(const DevFilter& d, const KeyHash& kh, uint32_t* map,
+                             uint32_t& ev, uint32_t& vt, uint64_t& vb,
+                             EvictCounters& ec) {
+  ev = 0;
+  if (d.max_ev == 0) {
+    vt = kh.fp;
+    vb = kh.i1;
+    return EV_FAIL;
+  }
+  Chain<G> c = chain_start<G>(d, kh);
+  int r;
+  do {
+    r = evict_round_map<G>(d, c, map, vt, vb, ec);
   } while (r == ROUND_CONTINUE);
   ev = c.ev;
   return r;

@@ -15,17 +15,32 @@ namespace cfk {
 // Keys per staging chunk of the host-buffer calls (default).
 constexpr uint64_t kDefaultStage = 1ull << 24;
 
-// Staging slots of the host-buffer calls: chunk c uses slot c mod
-// kStageSlots, so the copy of chunk c + kStageSlots - 1 can start while
-// chunk c runs; the host-to-device copies then follow one another without
-// waiting for flags to come back (a copy started on an idle link ran at
-// half its rate).
-constexpr int kStageSlots = 4;
+// Staging slots of the host-buffer calls, used in turn (across calls too):
+// the copies of the next kStageSlots - 1 chunks can run while a chunk's
+// kernels run, so the host-to-device copies follow one another without
+// waiting (a copy started on an idle link ran at half its rate).  Eight
+// slots of 2^25 keys hold a whole 2^28-key sliced pass, so the next pass's
+// keys can cross the link while the current pass finishes.
+constexpr int kStageSlots = 8;
 
 struct Stage {
   uint64_t* keys = nullptr;
+  cudaEvent_t in_done = nullptr, comp_done = nullptr;
+  bool used = false;  // comp_done has been recorded
+};
+
+// Flags of the host-buffer calls are gathered on the device for several
+// staging chunks and copied back in one piece per group of about
+// kFlagGroupBytes: many small device-to-host copies were measured to run at
+// a fraction of the link's rate on some boxes (32 MiB pieces at 44 GB/s
+// where 1 GiB copies ran at 194 GB/s).  Two groups alternate, so that the
+// kernels of one group overlap the copy of the other.
+constexpr uint64_t kFlagGroupBytes = 256ull << 20;
+struct FlagGroup {
   uint8_t* flags = nullptr;
-  cudaEvent_t in_done = nullptr, comp_done = nullptr, out_done = nullptr;
+  uint64_t cap = 0;  // bytes
+  cudaEvent_t comp_done = nullptr, out_done = nullptr;
+  bool used = false;  // out_done has been recorded
 };
 
 // Per-filter call ordering: the event of the filter's last operation and the
@@ -98,6 +113,10 @@ struct cf_filter {
   uint64_t queue_cap = 0;
   uint64_t stage_chunk = cfk::kDefaultStage;
   cfk::Stage stage[cfk::kStageSlots];
+  cfk::FlagGroup fgroup[2];
+  uint64_t group_chunks = 1;  // staging chunks per flag group
+  uint32_t next_slot = 0;     // staging slot and flag group used next
+  uint32_t next_group = 0;
   cudaStream_t s_in = nullptr, s_out = nullptr;
   bool stage_ready = false;
   cfk::FilterTimer* timer = nullptr;  // non-null while kernel timing is on
@@ -108,5 +127,10 @@ struct cf_filter {
   cfk::SliceBufs sb{};
   uint64_t sb_cap = 0;                 // keys the scratch is sized for
   void* sb_mem = nullptr;
+  // Full-bucket map of the eviction loop (cf_set_eviction_map): mode,
+  // least queued keys, and the map itself (allocated on first use).
+  int map_mode = 1;                    // 0 off, 1 automatic, 2 always
+  uint64_t map_min_queue = 0;          // 0: automatic rule
+  uint32_t* fullmap = nullptr;
 };
 

@@ -100,7 +100,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
                                             const uint32_t (&bkt)[K],
                                             const uint32_t (&tag)[K],
                                             const bool (&act)[K],
-                                            int (&res)[K]) {
+                                            int (&res)[K], uint32_t& first) {
   using W = typename G::Word;
   W cur[K];
   bool live[K];
@@ -116,7 +116,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
     const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
     if (live[k] && !zero_lanes<G>(cur[k] ^ pat)) live[k] = false;
   }
-  for (int round = 0; round < kMaxCas; ++round) {
+  for (uint32_t round = 0; round < cas_bound(d); ++round) {
     W old[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -136,6 +136,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
         live[k] = false;
         continue;
       }
+      note_cas_fail(d, round, first);
       cur[k] = old[k];
       const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
       if (!zero_lanes<G>(cur[k] ^ pat)) {
@@ -155,7 +156,8 @@ template <class G, int K, bool INSERT>
 __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
                                             const uint32_t (&bkt)[K],
                                             const uint32_t (&tag)[K],
-                                            const bool (&act)[K], int (&res)[K]) {
+                                            const bool (&act)[K], int (&res)[K],
+                                            uint32_t& first) {
   using W = typename G::Word;
   Bucket<G> bk[K];
   W cur[K];
@@ -184,7 +186,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
     }
     if (pos[k] == G::kWpb) live[k] = false;
   }
-  for (int round = 0; round < kMaxCas; ++round) {
+  for (uint32_t round = 0; round < cas_bound(d); ++round) {
     W old[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -205,6 +207,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
         live[k] = false;
         continue;
       }
+      note_cas_fail(d, round, first);
       cur[k] = old[k];
       const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
       if (!zero_lanes<G>(cur[k] ^ pat)) {
@@ -239,11 +242,12 @@ template <class G, int K, bool INSERT>
 __device__ __forceinline__ void cas_many(const DevFilter& d,
                                          const uint32_t (&bkt)[K],
                                          const uint32_t (&tag)[K],
-                                         const bool (&act)[K], int (&res)[K]) {
+                                         const bool (&act)[K], int (&res)[K],
+                                         uint32_t& first) {
   if constexpr (G::kWpb == 1)
-    cas_many_1w<G, K, INSERT>(d, bkt, tag, act, res);
+    cas_many_1w<G, K, INSERT>(d, bkt, tag, act, res, first);
   else
-    cas_many_nw<G, K, INSERT>(d, bkt, tag, act, res);
+    cas_many_nw<G, K, INSERT>(d, bkt, tag, act, res, first);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +259,7 @@ __device__ __forceinline__ void cas_many(const DevFilter& d,
 // ---------------------------------------------------------------------------
 struct TileCounts {
   uint32_t ok = 0, fail = 0, cont = 0;
+  uint32_t cas_first = 0;  // failed first CAS attempts (note_cas_fail)
 };
 
 // Appends key indices to a filter's eviction queue: the K keys of every
@@ -310,7 +315,7 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
     bkt[k] = kh.i1;
     tag[k] = kh.fp;
   }
-  cas_many<G, K, true>(d, bkt, tag, valid, r1);
+  cas_many<G, K, true>(d, bkt, tag, valid, r1, c.cas_first);
   // Alternate buckets only for the keys whose primary bucket was full.
   bool act[K];
 #pragma unroll
@@ -321,7 +326,7 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
       tag[k] |= G::kChoice;
     }
   }
-  cas_many<G, K, true>(d, bkt, tag, act, r2);
+  cas_many<G, K, true>(d, bkt, tag, act, r2, c.cas_first);
   bool need[K];
   uint32_t qidx[K];
 #pragma unroll
@@ -408,7 +413,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
     bkt[k] = kh.i1;
     tag[k] = kh.fp;
   }
-  cas_many<G, K, false>(d, bkt, tag, valid, r1);
+  cas_many<G, K, false>(d, bkt, tag, valid, r1, c.cas_first);
   bool act[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -418,7 +423,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
       tag[k] |= G::kChoice;
     }
   }
-  cas_many<G, K, false>(d, bkt, tag, act, r2);
+  cas_many<G, K, false>(d, bkt, tag, act, r2, c.cas_first);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (!valid[k]) continue;
@@ -474,6 +479,8 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
   block_add(&d.ctrl->insert_ok, c.ok);
   block_add(&d.ctrl->insert_fail, c.cont);
   block_add(&d.ctrl->contention, c.cont);
+  block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 
 // Insert, phase 2: the eviction loop for every queued key.  Chains have
@@ -494,12 +501,17 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
 // load the key, load the first bucket.  When the chain ends, the next one
 // starts from the prepared words at once.  (The words may be a few rounds
 // old: a stale word only costs the CAS that detects it.)
+//
+// map / min_q: when map is given and at least min_q keys are queued, the
+// BFS rounds ask the full-bucket map (built by k_fullmap just before, on the
+// same rule) whether candidates' alternate buckets are open (bfs_round_map).
 template <class G, bool FROM_HASH = false>
 __global__ void __launch_bounds__(kBlock, CF_MINB_EVICT)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
                uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
-               const uint32_t* __restrict__ queue) {
+               const uint32_t* __restrict__ queue, uint32_t* map, uint32_t min_q) {
   const uint32_t qn = *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
+  const bool use_map = map != nullptr && qn >= min_q && d.eviction == 0;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t n_warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
@@ -561,7 +573,8 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
     if (active) {
       uint32_t vt = 0;
       uint64_t vb = 0;
-      const int r = evict_round<G, EvictFW<G>::value>(d, c, vt, vb, ec);
+      const int r = use_map ? evict_round_map<G>(d, c, map, vt, vb, ec)
+                            : evict_round<G, EvictFW<G>::value>(d, c, vt, vb, ec);
       if (r != ROUND_CONTINUE) {
         if (r != EV_OK) log_victim(d, vt, vb);
         if (flags) st_flag(flags + idx, uint8_t(r));
@@ -579,6 +592,7 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
   block_add(&d.ctrl->rollbacks, ec.rollbacks);
   block_add(&d.ctrl->rollback_lost, ec.rollback_lost);
   block_add(&d.ctrl->contention, ec.contention);
+  block_add(&d.ctrl->cas_retry[0], ec.cas_first);
   if (ec.contention) atomicOr(&d.ctrl->error_word, 1u);
   if (threadIdx.x == 0) {
     __threadfence();
@@ -591,13 +605,50 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
   }
 }
 
+// The full-bucket map of the eviction loop (see bfs_round_map): bit j set
+// iff bucket j has no empty slot, from one pass over the table.  A warp
+// reads 32 consecutive buckets (one per lane, coalesced) and writes their 32
+// bits as one word.  Runs only when at least min_q keys are queued, the
+// rule k_insert_evict applies to use the map.
+template <class G>
+__global__ void __launch_bounds__(kBlock)
+k_fullmap(DevFilter d, uint32_t* __restrict__ map, uint32_t min_q) {
+  const uint32_t qn = *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
+  if (qn < min_q || d.eviction != 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&d.ctrl->map_builds, 1ull);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gw = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t groups = (d.m + 31) >> 5;
+  for (uint64_t g = gw; g < groups; g += nw) {
+    const uint64_t j = (g << 5) + lane;
+    bool full = false;
+    if (j < d.m) full = !has_empty<G>(load_bucket<G, true>(bucket_ptr<G>(d, j)));
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, full);
+    if (lane == 0) map[g] = bits;
+  }
+}
+
+// TryInsert that keeps an exact full-bucket map (one thread only).
+template <class G>
+__device__ __forceinline__ int try_insert_mapped(const DevFilter& d, uint64_t j,
+                                                 uint32_t tag, uint32_t* map) {
+  Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
+  uint32_t first = 0;  // one thread: no CAS ever fails
+  const int r = try_insert_loaded<G>(d, j, tag, bk, first);
+  if (map && r == TI_OK && !has_empty<G>(bk)) map_set(map, j);
+  return r;
+}
+
 // The whole insert of Alg. 1 + Sec. 4.6.1, one thread, keys in order
 // (deterministic placement; used to compare with a sequential
-// implementation bit for bit).
+// implementation bit for bit).  With a map (built from the table just
+// before and kept exact here), the BFS rounds take their candidates'
+// open / full answers from it (bfs_round_map).
 template <class G>
 __global__ void k_insert_serial(DevFilter d, const uint64_t* __restrict__ keys,
                                 uint64_t n, uint8_t* __restrict__ flags,
-                                uint32_t* __restrict__ evout) {
+                                uint32_t* __restrict__ evout, uint32_t* map) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   EvictCounters ec;
   unsigned long long n_ok = 0, n_fail = 0, n_ev = 0;
@@ -606,7 +657,7 @@ __global__ void k_insert_serial(DevFilter d, const uint64_t* __restrict__ keys,
     uint32_t ev = 0, vt = 0;
     uint64_t vb = 0;
     int r;
-    const int a = try_insert<G>(d, kh.i1, kh.fp);
+    const int a = try_insert_mapped<G>(d, kh.i1, kh.fp, map);
     if (a == TI_OK) {
       r = EV_OK;
     } else if (a == TI_CONTENTION) {
@@ -614,13 +665,15 @@ __global__ void k_insert_serial(DevFilter d, const uint64_t* __restrict__ keys,
       vt = kh.fp;
       vb = kh.i1;
     } else {
-      const int b = try_insert<G>(d, kh.i2, kh.fp | G::kChoice);
+      const int b = try_insert_mapped<G>(d, kh.i2, kh.fp | G::kChoice, map);
       if (b == TI_OK) {
         r = EV_OK;
       } else if (b == TI_CONTENTION) {
         r = EV_CONTENTION;
         vt = kh.fp | G::kChoice;
         vb = kh.i2;
+      } else if (map && d.eviction == 0) {
+        r = evict_key_map<G>(d, kh, map, ev, vt, vb, ec);
       } else {
         r = evict_key<G>(d, kh, ev, vt, vb, ec);
       }
@@ -665,6 +718,8 @@ k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
   block_add(&d.ctrl->remove_ok, c.ok);
   block_add(&d.ctrl->remove_fail, c.fail + c.cont);
   block_add(&d.ctrl->contention, c.cont);
+  block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 
 // Hash export for tests: fp, i1, i2 per key.
@@ -738,7 +793,15 @@ enum KernelKind : int {
   KK_SLICE_PROBE1 = 5,  // ... bucket i1 pass
   KK_SLICE_PROBE2 = 6,  // ... bucket i2 pass
   KK_SLICE_MERGE = 7,   // ... merge + out (results back to key order)
-  KK_NUM = 8
+  KK_EVICT_MAP = 8,     // full-bucket map of the eviction loop
+  KK_NUM = 9
+};
+
+// The full-bucket map of one insert call: bits (m/32 words, rounded up) or
+// null, and the least number of queued keys for which it is built and used.
+struct EvictMap {
+  uint32_t* bits = nullptr;
+  uint32_t min_q = 0;
 };
 struct KernelTimer {
   virtual void begin(int kind, cudaStream_t s) = 0;
@@ -772,9 +835,20 @@ struct Launch {
     if (t) t->end(KK_REMOVE, s);
     return cudaGetLastError();
   }
+  // The full-bucket map before an eviction launch (a no-op launch unless
+  // at least em.min_q keys are queued).
+  static cudaError_t fullmap(const DevFilter& d, const EvictMap& em, cudaStream_t s,
+                             KernelTimer* t) {
+    if (!em.bits) return cudaSuccess;
+    auto fm = k_fullmap<G>;
+    if (t) t->begin(KK_EVICT_MAP, s);
+    fm<<<persistent_grid(fm, d.m, kBlock), kBlock, 0, s>>>(d, em.bits, em.min_q);
+    if (t) t->end(KK_EVICT_MAP, s);
+    return cudaGetLastError();
+  }
   static cudaError_t insert_chunk(const DevFilter& d, const uint64_t* keys,
                                   uint32_t n, uint8_t* flags, uint32_t* evout,
-                                  uint32_t* queue, cudaStream_t s,
+                                  uint32_t* queue, const EvictMap& em, cudaStream_t s,
                                   KernelTimer* t) {
     auto f1 = l2_table(d) ? k_insert_direct<G, KM, MINB_L2> : k_insert_direct<G, KM>;
     if (t) t->begin(KK_INSERT_DIRECT, s);
@@ -783,17 +857,24 @@ struct Launch {
     if (t) t->end(KK_INSERT_DIRECT, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    e = fullmap(d, em, s, t);
+    if (e != cudaSuccess) return e;
     auto f2 = k_insert_evict<G>;
     if (t) t->begin(KK_INSERT_EVICT, s);
     f2<<<evict_grid(reinterpret_cast<const void*>(f2)), kBlock, 0, s>>>(
-        d, keys, flags, evout, queue);
+        d, keys, flags, evout, queue, em.bits, em.min_q);
     if (t) t->end(KK_INSERT_EVICT, s);
     return cudaGetLastError();
   }
+  // map: null, or a full-bucket map to build now and keep exact (BFS only).
   static cudaError_t insert_serial(const DevFilter& d, const uint64_t* keys,
                                    uint64_t n, uint8_t* flags, uint32_t* evout,
-                                   cudaStream_t s) {
-    k_insert_serial<G><<<1, 32, 0, s>>>(d, keys, n, flags, evout);
+                                   uint32_t* map, cudaStream_t s) {
+    if (map) {
+      cudaError_t e = fullmap(d, EvictMap{map, 0}, s, nullptr);
+      if (e != cudaSuccess) return e;
+    }
+    k_insert_serial<G><<<1, 32, 0, s>>>(d, keys, n, flags, evout, map);
     return cudaGetLastError();
   }
   static cudaError_t hash(const DevFilter& d, const uint64_t* keys, uint64_t n,
@@ -817,17 +898,25 @@ struct Ops {
   cudaError_t (*remove)(const DevFilter&, const uint64_t*, uint64_t, uint8_t*,
                         cudaStream_t, KernelTimer*);
   cudaError_t (*insert_chunk)(const DevFilter&, const uint64_t*, uint32_t,
-                              uint8_t*, uint32_t*, uint32_t*, cudaStream_t,
-                              KernelTimer*);
+                              uint8_t*, uint32_t*, uint32_t*, const EvictMap&,
+                              cudaStream_t, KernelTimer*);
   cudaError_t (*insert_serial)(const DevFilter&, const uint64_t*, uint64_t,
-                               uint8_t*, uint32_t*, cudaStream_t);
+                               uint8_t*, uint32_t*, uint32_t*, cudaStream_t);
   cudaError_t (*hash)(const DevFilter&, const uint64_t*, uint64_t, uint32_t*,
                       uint64_t*, uint64_t*, cudaStream_t);
   cudaError_t (*count)(const DevFilter&, unsigned long long*, cudaStream_t);
   // Slice-partitioned insert / contains / remove of one chunk (op: 0 / 1 / 2).
   cudaError_t (*sliced)(const DevFilter&, int, const uint64_t*, uint64_t,
-                        uint8_t*, const SliceBufs&, uint32_t*, cudaStream_t,
-                        KernelTimer*);
+                        uint8_t*, const SliceBufs&, uint32_t*, const EvictMap&,
+                        cudaStream_t, KernelTimer*);
+  // The same pass in parts: begin, scatter of keys [dst_off, dst_off + n)
+  // (repeatable), finish (see SliceLaunch).
+  cudaError_t (*sliced_begin)(const SliceBufs&, cudaStream_t);
+  cudaError_t (*sliced_scatter)(const DevFilter&, const uint64_t*, uint64_t, uint64_t,
+                                int, const SliceBufs&, cudaStream_t, KernelTimer*);
+  cudaError_t (*sliced_finish)(const DevFilter&, int, uint64_t, uint8_t*,
+                               const SliceBufs&, uint32_t*, const EvictMap&,
+                               cudaStream_t, KernelTimer*);
 };
 
 // ops_for<G>() (the table of one geometry) is defined in cf_slice.cuh.

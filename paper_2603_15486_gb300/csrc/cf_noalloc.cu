@@ -3,14 +3,14 @@
 //
 // cf_insert keeps its eviction work queue (4 bytes per key) in memory the
 // library cudaMalloc's on a filter's first large insert.  This entry point
-// runs the same two kernels with the queue in a fixed array compiled into
-// the library instead, so it calls no cudaMalloc or cudaFree.  The array is
-// a file-scope __device__ variable: every GPU that loads the library holds
-// it (4 MiB) until the process exits.
+// runs the plain two-kernel insert (direct insertion, then the eviction
+// loop) with the queue in a fixed array compiled into the library instead,
+// so it calls no cudaMalloc or cudaFree.  The array is a file-scope
+// __device__ variable: every GPU that loads the library holds it (4 MiB)
+// until the process exits.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "cf.h"
 #include "cf_internal.h"
@@ -19,26 +19,22 @@ namespace {
 
 static __device__ __align__(256) uint32_t g_noalloc_queue[CF_NOALLOC_MAX_KEYS];
 
-// Device address of g_noalloc_queue, looked up once per device.  In host
-// code the symbol's name is only a host-side stand-in; the kernels must be
-// given this address.
-std::mutex g_mu;
-uint32_t* g_queue_dev[64] = {};
-
-cf_status queue_for_device(int dev, uint32_t** out) {
-  if (dev < 0 || dev >= 64) return CF_ENOTSUP;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_queue_dev[dev]) {
-    uint32_t* ptr = nullptr;
-    const cudaError_t e =
-        cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_queue);
-    if (e != cudaSuccess) {
-      cfk::set_error("cudaGetSymbolAddress(g_noalloc_queue)", e);
-      return CF_ECUDA;
-    }
-    g_queue_dev[dev] = ptr;
+// Device address of g_noalloc_queue in the current device's context.  In
+// host code the symbol's name is only a host-side stand-in; the kernels
+// must be given this address.  It is looked up on every call (a host-side
+// table lookup once the library's device code is loaded): a context that
+// was torn down and rebuilt (cudaDeviceReset) places the array anew, and a
+// cached address would then point at memory the context no longer maps.
+cf_status queue_address(uint32_t** out) {
+  uint32_t* ptr = nullptr;
+  const cudaError_t e =
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_queue);
+  if (e != cudaSuccess || ptr == nullptr) {
+    cfk::set_error("cudaGetSymbolAddress(g_noalloc_queue)",
+                   e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    return CF_ECUDA;
   }
-  *out = g_queue_dev[dev];
+  *out = ptr;
   return CF_OK;
 }
 
@@ -67,13 +63,13 @@ extern "C" cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys,
     return CF_EINVAL;
   }
   uint32_t* queue = nullptr;
-  cf_status st = queue_for_device(dev, &queue);
+  cf_status st = queue_address(&queue);
   if (st != CF_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = cfk::order_on(f, s);
   if (st != CF_OK) return st;
-  e = f->ops->insert_chunk(f->d, keys, uint32_t(n), out_flags, nullptr, queue, s,
-                           f->timer);
+  e = f->ops->insert_chunk(f->d, keys, uint32_t(n), out_flags, nullptr, queue,
+                           cfk::EvictMap{}, s, f->timer);
   if (e != cudaSuccess) {
     cfk::set_error("cf_insert_noalloc launch", e);
     return CF_ECUDA;

@@ -24,55 +24,6 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// One 8-byte load with a given cache-operator flavour.
-template <int FL>
-__device__ __forceinline__ unsigned long long ld_flavour(const unsigned long long* p) {
-  unsigned long long v;
-  if constexpr (FL == 0)
-    asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 1)
-    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 2)
-    asm volatile("ld.global.cs.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 3)
-    asm volatile("ld.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 4)
-    asm volatile("ld.global.lu.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 5)
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 6)
-    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 7)
-    asm volatile("ld.global.nc.L1::no_allocate.L2::64B.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else if constexpr (FL == 8)
-    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  else
-    asm volatile("atom.global.or.b64 %0, [%1], 0;" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// 8-byte random loads with flavour FL (see cf_probe_gather_flavour), KP in
-// flight per thread.
-template <int FL, int KP>
-__global__ void __launch_bounds__(kProbeBlock)
-k_gather_flavour(const unsigned long long* __restrict__ buf, uint64_t n_slots,
-                 uint64_t n_access, uint64_t seed, unsigned long long* sink) {
-  unsigned long long acc = 0;
-  const uint64_t tid = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
-  const uint64_t nth = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t base = tid * KP; base < n_access; base += nth * KP) {
-    unsigned long long v[KP];
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-      const uint64_t slot = mix64(seed + base + k) & (n_slots - 1);
-      v[k] = (base + k < n_access) ? ld_flavour<FL>(buf + slot) : 0ull;
-    }
-#pragma unroll
-    for (int k = 0; k < KP; ++k) acc ^= v[k];
-  }
-  if (acc == 0x5EEDull) atomicAdd(sink, 1ull);
-}
-
 // Each thread issues kProbeK independent loads of `W` 64-bit words at
 // random W*8-aligned offsets, then folds them into one value per thread.
 // n_slots is a power of two (the offset is a mask of a 64-bit mix).
@@ -133,48 +84,9 @@ cudaError_t launch_gather_k(const unsigned long long* p, uint64_t slots,
   }
 }
 
-template <int FL>
-cudaError_t launch_flavour(const unsigned long long* p, uint64_t slots,
-                           uint64_t n_access, uint64_t seed,
-                           unsigned long long* sink, cudaStream_t s) {
-  auto fn = k_gather_flavour<FL, 8>;
-  const int occ = cfk::cached_occupancy(reinterpret_cast<const void*>(fn), kProbeBlock);
-  const uint64_t cap = uint64_t(cfk::device_sm_count()) * uint64_t(occ);
-  uint64_t want = (n_access + kProbeBlock * 8 - 1) / (kProbeBlock * 8);
-  fn<<<unsigned(want < cap ? want : cap), kProbeBlock, 0, s>>>(p, slots, n_access, seed, sink);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 extern "C" {
-
-cf_status cf_probe_gather_flavour(const void* buf, uint64_t bytes,
-                                  uint64_t n_access, uint32_t flavour,
-                                  uint64_t seed, unsigned long long* sink,
-                                  void* stream) {
-  if (!buf || !sink || flavour > 9) return CF_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(buf) & 31) != 0) return CF_EINVAL;
-  uint64_t slots = bytes / 8;
-  if (slots == 0 || n_access == 0) return CF_EINVAL;
-  while (slots & (slots - 1)) slots &= slots - 1;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const unsigned long long* p = static_cast<const unsigned long long*>(buf);
-  cudaError_t e;
-  switch (flavour) {
-    case 0: e = launch_flavour<0>(p, slots, n_access, seed, sink, s); break;
-    case 1: e = launch_flavour<1>(p, slots, n_access, seed, sink, s); break;
-    case 2: e = launch_flavour<2>(p, slots, n_access, seed, sink, s); break;
-    case 3: e = launch_flavour<3>(p, slots, n_access, seed, sink, s); break;
-    case 4: e = launch_flavour<4>(p, slots, n_access, seed, sink, s); break;
-    case 5: e = launch_flavour<5>(p, slots, n_access, seed, sink, s); break;
-    case 6: e = launch_flavour<6>(p, slots, n_access, seed, sink, s); break;
-    case 7: e = launch_flavour<7>(p, slots, n_access, seed, sink, s); break;
-    case 8: e = launch_flavour<8>(p, slots, n_access, seed, sink, s); break;
-    default: e = launch_flavour<9>(p, slots, n_access, seed, sink, s); break;
-  }
-  return e == cudaSuccess ? CF_OK : CF_ECUDA;
-}
 
 cf_status cf_probe_gather(const void* buf, uint64_t bytes, uint64_t n_access,
                           uint32_t access_bytes, uint32_t loads_per_thread,

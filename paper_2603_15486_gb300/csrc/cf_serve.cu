@@ -10,12 +10,20 @@
 //   4. fills every free wave slot: round-robin over the live filters with
 //      no work in flight, it takes each one's oldest queued requests of one
 //      kind, up to the wave's item and key limits, and launches them as one
-//      multi-filter launch on the slot's own stream.
+//      multi-filter launch on the slot's own stream (a wave of one query or
+//      delete runs the single-filter kernel instead, which has less to set
+//      up than the multi-filter launch).
 // Several waves are on the GPU at once, so requests that arrive while
 // others run start as soon as a slot frees up, and their kernels overlap.
+// Latency: while waves are on the GPU the scheduler polls their events
+// without sleeping, and after any activity it keeps polling for new
+// requests for kSpinIdle before it sleeps on its condition variable (a
+// sleep and wake-up costs tens of microseconds, more than a small
+// request's kernels).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -28,6 +36,10 @@
 #include "cf_internal.h"
 
 namespace {
+
+// How long the scheduler keeps polling for new requests after its last
+// activity before it sleeps.
+constexpr double kSpinIdle = 2e-3;
 
 double now_s() {
   return std::chrono::duration<double>(
@@ -85,6 +97,7 @@ struct cf_server {
   uint64_t next_req = 1, submitted = 0, completed = 0, n_waves = 0, late = 0;
   uint64_t keys_done = 0;
   bool stop = false;
+  std::atomic<uint64_t> kicks{0};  // bumped by every submit / add / remove
   std::thread worker;
 };
 
@@ -179,6 +192,10 @@ bool admit(cf_server* s) {
       s->cv_done.notify_all();
       continue;
     }
+    // Waves of one query or delete run the single-filter kernels; keep them
+    // on the plain path, which needs no scratch memory (no allocation, and
+    // so no implicit device synchronisation, inside the scheduler).
+    cf_set_slicing(f, 0, 0, 0);
     fs->f = f;
     fs->state = CF_FILTER_LIVE;
     s->used += fs->bytes;
@@ -217,16 +234,26 @@ bool fill_wave(cf_server* s, WaveSlot& w) {
 }
 
 cf_status launch_wave(cf_server* s, WaveSlot& w) {
-  w.items.resize(w.reqs.size());
-  for (size_t i = 0; i < w.reqs.size(); ++i) {
-    const cf_request& r = w.reqs[i]->r;
-    w.items[i] = cf_batch_item{s->filters[r.filter_id]->f, r.keys, r.n, r.out_flags,
-                               r.op, 0};
+  cf_status st = CF_OK;
+  const cf_request& r0 = w.reqs[0]->r;
+  if (w.reqs.size() == 1 && r0.op != CF_OP_INSERT) {
+    // One query or delete: the single-filter kernel on the slot's stream
+    // (the filter's call ordering holds across the two launch forms).
+    cf_filter* f = s->filters[r0.filter_id]->f;
+    st = r0.op == CF_OP_CONTAINS ? cf_contains(f, r0.keys, r0.n, r0.out_flags, w.stream)
+                                 : cf_remove(f, r0.keys, r0.n, r0.out_flags, w.stream);
+  } else {
+    w.items.resize(w.reqs.size());
+    for (size_t i = 0; i < w.reqs.size(); ++i) {
+      const cf_request& r = w.reqs[i]->r;
+      w.items[i] = cf_batch_item{s->filters[r.filter_id]->f, r.keys, r.n, r.out_flags,
+                                 r.op, 0};
+    }
+    st = cf_batch_set(w.plan, w.items.data(), uint32_t(w.items.size()));
+    if (st == CF_OK)
+      st = s->cfg.use_graphs ? cf_batch_graph_launch(w.plan, w.stream)
+                             : cf_batch_launch(w.plan, w.stream);
   }
-  cf_status st = cf_batch_set(w.plan, w.items.data(), uint32_t(w.items.size()));
-  if (st == CF_OK)
-    st = s->cfg.use_graphs ? cf_batch_graph_launch(w.plan, w.stream)
-                           : cf_batch_launch(w.plan, w.stream);
   if (st == CF_OK && cudaEventRecord(w.done, w.stream) != cudaSuccess) st = CF_ECUDA;
   const double t = now_s();
   if (st != CF_OK) {
@@ -256,7 +283,9 @@ bool has_queued(const cf_server* s) {
 void worker_main(cf_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
+  double last_active = now_s();
   for (;;) {
+    const uint64_t kicks = s->kicks.load(std::memory_order_acquire);
     bool progressed = retire_waves(s);
     progressed |= close_filters(s);
     progressed |= admit(s);
@@ -269,11 +298,23 @@ void worker_main(cf_server* s) {
     bool busy = false;
     for (const auto& w : s->waves) busy = busy || w.busy;
     if (s->stop && !busy && !has_queued(s)) break;
-    if (!progressed) {
-      if (busy)
-        s->cv.wait_for(lk, std::chrono::microseconds(10));
-      else
-        s->cv.wait_for(lk, std::chrono::milliseconds(50));
+    if (progressed) {
+      last_active = now_s();
+      continue;
+    }
+    // Nothing to do right now.  Poll (with the lock released, so that
+    // submitters get in) while waves are on the GPU or shortly after the
+    // last activity; otherwise sleep until a submit wakes us.
+    if (busy || now_s() - last_active < kSpinIdle) {
+      lk.unlock();
+      for (int i = 0; i < 64 && s->kicks.load(std::memory_order_acquire) == kicks; ++i)
+        std::this_thread::yield();
+      lk.lock();
+      if (busy) last_active = now_s();
+    } else {
+      s->cv.wait_for(lk, std::chrono::milliseconds(50),
+                     [&] { return s->kicks.load(std::memory_order_acquire) != kicks || s->stop; });
+      last_active = now_s();
     }
   }
 }
@@ -294,6 +335,7 @@ cf_status submit_locked(cf_server* s, const cf_request* r, int64_t trace_index,
   q->trace_index = trace_index;
   it->second->q.push_back(q);
   s->submitted++;
+  s->kicks.fetch_add(1, std::memory_order_release);
   if (id) *id = q->id;
   return CF_OK;
 }
@@ -333,6 +375,7 @@ cf_status cf_server_destroy(cf_server* s) {
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->stop = true;
+      s->kicks.fetch_add(1, std::memory_order_release);
     }
     s->cv.notify_all();
     s->worker.join();
@@ -365,6 +408,7 @@ cf_status cf_server_add_filter(cf_server* s, const cf_config* cfg, uint32_t* fil
   s->order.push_back(fs->id);
   s->admission.push_back(fs->id);
   *filter_id = fs->id;
+  s->kicks.fetch_add(1, std::memory_order_release);
   s->cv.notify_all();
   return CF_OK;
 }
@@ -375,6 +419,7 @@ cf_status cf_server_remove_filter(cf_server* s, uint32_t filter_id) {
   auto it = s->filters.find(filter_id);
   if (it == s->filters.end()) return CF_EINVAL;
   it->second->remove_requested = true;
+  s->kicks.fetch_add(1, std::memory_order_release);
   s->cv.notify_all();
   return CF_OK;
 }

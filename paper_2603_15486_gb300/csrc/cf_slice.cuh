@@ -428,7 +428,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
         for (int k = 0; k < K; ++k)
           res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
       } else {
-        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
+        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res, c.cas_first);
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -495,6 +495,8 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
     block_add(&d.ctrl->remove_fail, c.cont);
     block_add(&d.ctrl->contention, c.cont);
   }
+  if constexpr (OP != SOP_CONTAINS) block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -585,7 +587,7 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
           if (valid[k] && want_flags)
             st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
       } else {
-        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res);
+        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res, c.cas_first);
         bool to_queue[K];
         uint32_t qidx[K];
 #pragma unroll
@@ -624,6 +626,8 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
     block_add(&d.ctrl->remove_fail, c.fail + c.cont);
     block_add(&d.ctrl->contention, c.cont);
   }
+  if constexpr (OP != SOP_CONTAINS) block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -783,26 +787,38 @@ struct SliceLaunch {
     return cudaGetLastError();
   }
 
-  static cudaError_t run(const DevFilter& d, int op, const uint64_t* keys,
-                         uint64_t n, uint8_t* flags, const SliceBufs& sb,
-                         uint32_t* queue, cudaStream_t s, KernelTimer* t) {
+  // A pass in three parts, so that a pass's keys can arrive in pieces (the
+  // host-buffer calls scatter each staging chunk as its copy lands):
+  // begin (counters to zero), scatter (any number of times, each for keys
+  // [dst_off, dst_off + n) of the pass), finish (everything after the split).
+  static cudaError_t begin(const SliceBufs& sb, cudaStream_t s) {
+    // fill1 and fill2 (and the tile counters after it) share one range.
+    const size_t ctr_bytes = reinterpret_cast<const char*>(
+                                 sb.fill2 + (sb.n_slices + kFill2Extra) * kCtrStride) -
+                             reinterpret_cast<const char*>(sb.fill1);
+    return cudaMemsetAsync(sb.fill1, 0, ctr_bytes, s);
+  }
+
+  static cudaError_t scatter(const DevFilter& d, const uint64_t* keys, uint64_t n,
+                             uint64_t dst_off, int want, const SliceBufs& sb,
+                             cudaStream_t s, KernelTimer* t) {
+    auto fs = k_slice_scatter<G, U>;
+    const size_t smem = size_t(8) * kBlock * U + size_t(16) * sb.n_slices;
+    cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(fs), smem);
+    if (e != cudaSuccess) return e;
+    if (t) t->begin(KK_SLICE_SPLIT, s);
+    fs<<<persistent_grid(fs, n, kBlock * U), kBlock, smem, s>>>(
+        d, keys, n, sb, want ? sb.dst + dst_off : nullptr);
+    if (t) t->end(KK_SLICE_SPLIT, s);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t finish(const DevFilter& d, int op, uint64_t n, uint8_t* flags,
+                            const SliceBufs& sb, uint32_t* queue, const EvictMap& em,
+                            cudaStream_t s, KernelTimer* t) {
     const int want = flags != nullptr;
     const uint32_t S = sb.n_slices;
-    if (t) t->begin(KK_SLICE_SPLIT, s);
-    // fill1 and fill2 (and the tile counters after it) share one range.
-    const size_t ctr_bytes = reinterpret_cast<const char*>(sb.fill2 + (S + kFill2Extra) * kCtrStride) -
-                             reinterpret_cast<const char*>(sb.fill1);
-    cudaError_t e = cudaMemsetAsync(sb.fill1, 0, ctr_bytes, s);
-    if (e != cudaSuccess) return e;
-    auto fs = k_slice_scatter<G, U>;
-    const size_t smem = size_t(8) * kBlock * U + size_t(16) * S;
-    e = smem_opt_in(reinterpret_cast<const void*>(fs), smem);
-    if (e != cudaSuccess) return e;
-    fs<<<persistent_grid(fs, n, kBlock * U), kBlock, smem, s>>>(d, keys, n, sb,
-                                                                want ? sb.dst : nullptr);
-    if (t) t->end(KK_SLICE_SPLIT, s);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     // All three operations take the query's K (8 for 8-byte buckets): the
     // bucket accesses hit L2 here, so the mutating passes are latency-bound
     // and want every key's load and CAS of a tile in flight together.
@@ -814,10 +830,12 @@ struct SliceLaunch {
       e = probes<SOP_INSERT, KMS>(d, sb, n, want, queue, s, t);
     if (e != cudaSuccess) return e;
     if (op == SOP_INSERT) {
+      e = Launch<G>::fullmap(d, em, s, t);
+      if (e != cudaSuccess) return e;
       auto fe = k_insert_evict<G, true>;
       if (t) t->begin(KK_INSERT_EVICT, s);
       fe<<<evict_grid(reinterpret_cast<const void*>(fe)), kBlock, 0, s>>>(
-          d, sb.rec2, want ? sb.f2 : nullptr, nullptr, queue);
+          d, sb.rec2, want ? sb.f2 : nullptr, nullptr, queue, em.bits, em.min_q);
       if (t) t->end(KK_INSERT_EVICT, s);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
@@ -831,13 +849,26 @@ struct SliceLaunch {
     if (t) t->end(KK_SLICE_MERGE, s);
     return cudaGetLastError();
   }
+
+  static cudaError_t run(const DevFilter& d, int op, const uint64_t* keys,
+                         uint64_t n, uint8_t* flags, const SliceBufs& sb,
+                         uint32_t* queue, const EvictMap& em, cudaStream_t s,
+                         KernelTimer* t) {
+    cudaError_t e = begin(sb, s);
+    if (e != cudaSuccess) return e;
+    e = scatter(d, keys, n, 0, flags != nullptr, sb, s, t);
+    if (e != cudaSuccess) return e;
+    return finish(d, op, n, flags, sb, queue, em, s, t);
+  }
 };
 
 template <class G>
 const Ops* ops_for() {
-  static const Ops o = {&Launch<G>::contains, &Launch<G>::remove,
+  static const Ops o = {&Launch<G>::contains,     &Launch<G>::remove,
                         &Launch<G>::insert_chunk, &Launch<G>::insert_serial,
-                        &Launch<G>::hash, &Launch<G>::count, &SliceLaunch<G>::run};
+                        &Launch<G>::hash,         &Launch<G>::count,
+                        &SliceLaunch<G>::run,     &SliceLaunch<G>::begin,
+                        &SliceLaunch<G>::scatter, &SliceLaunch<G>::finish};
   return &o;
 }
 

@@ -23,7 +23,14 @@ struct Ctrl {
   unsigned int done_blocks;  // last-block-done counter of the evict kernel
   unsigned int pad0;
   unsigned long long scratch_count;  // for cf_count_occupied
-  unsigned long long pad[19];
+  // Eviction launches that built and used the full-bucket map.
+  unsigned long long map_builds;
+  // CAS-retry histogram: failed CAS attempts by their retry depth within one
+  // loop (the attempt that failed was the r-th retry, r = 0 being the first
+  // attempt): bins r = 0, 1, 2-3, 4-7, 8-15, 16-63, 64 and more.  Bin k thus
+  // counts the loops that needed more than the retries of bins below it.
+  unsigned long long cas_retry[7];
+  unsigned long long pad[11];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
 
@@ -45,7 +52,7 @@ struct DevFilter {
   uint32_t victim_cap;
   uint32_t max_ev;
   uint32_t eviction;  // 0 BFS, 1 DFS
-  uint32_t pad;
+  uint32_t max_cas;   // bound of every CAS retry loop (attempts per word)
 };
 
 constexpr uint32_t kSliceMax = 1024;  // slices per table (shared-memory bins)

@@ -185,6 +185,20 @@ class CuckooFilter:
     def remove_host(self, keys, out=None, stream=None):
         return self._host_call(self._L.cf_remove_host, keys, out, "cf_remove_host", stream)
 
+    def insert_host_async(self, keys, out=None, stream=None):
+        """Asynchronous insert from host buffers: `out` (and `keys`) must stay
+        alive until `stream` synchronises."""
+        return self._host_call(self._L.cf_insert_host_async, keys, out,
+                               "cf_insert_host_async", stream)
+
+    def contains_host_async(self, keys, out=None, stream=None):
+        return self._host_call(self._L.cf_contains_host_async, keys, out,
+                               "cf_contains_host_async", stream)
+
+    def remove_host_async(self, keys, out=None, stream=None):
+        return self._host_call(self._L.cf_remove_host_async, keys, out,
+                               "cf_remove_host_async", stream)
+
     def set_staging_chunk(self, keys_per_chunk: int):
         check(self._L.cf_set_staging_chunk(self._h, int(keys_per_chunk)), "cf_set_staging_chunk")
 
@@ -196,13 +210,28 @@ class CuckooFilter:
               "cf_set_slicing")
 
     # ---- state -----------------------------------------------------------------
+    def set_eviction_map(self, mode: str = "auto", min_queue: int = 0):
+        """Full-bucket map of the eviction loop: "off", "auto" or "always"
+        (cf_set_eviction_map)."""
+        modes = {"off": 0, "auto": 1, "always": 2}
+        check(self._L.cf_set_eviction_map(self._h, modes[mode], int(min_queue)),
+              "cf_set_eviction_map")
+
+    def set_cas_limit(self, limit: int = 0):
+        """Test knob: bound of the CAS retry loops (0 = default 4096)."""
+        check(self._L.cf_debug_set_cas_limit(self._h, int(limit)), "cf_debug_set_cas_limit")
+
     def clear(self, stream=None):
         check(self._L.cf_clear(self._h, _stream_handle(stream)), "cf_clear")
 
     def stats(self, stream=None) -> dict:
         st = CfStats()
         check(self._L.cf_stats(self._h, ctypes.byref(st), _stream_handle(stream)), "cf_stats")
-        return {n: int(getattr(st, n)) for n, _ in CfStats._fields_}
+        out = {}
+        for n, _ in CfStats._fields_:
+            v = getattr(st, n)
+            out[n] = [int(x) for x in v] if n == "cas_retry" else int(v)
+        return out
 
     def victims(self, stream=None):
         cnt = ctypes.c_uint64()

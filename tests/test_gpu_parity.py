@@ -304,6 +304,48 @@ def test_contention_stress_tiny_tables(cf, m, eviction):
     assert st["occupancy"] <= m * b
 
 
+@pytest.mark.parametrize("m", [1 << 4, 1 << 6])
+@pytest.mark.parametrize("eviction", ["bfs", "dfs"])
+@pytest.mark.parametrize("slicing", ["off", "always"])
+def test_cas_limit_runs_out(cf, m, eviction, slicing):
+    """With the CAS retry bound lowered to one attempt, the duplicate-heavy
+    stress makes the bounded loops run out: those keys end with
+    CF_FLAG_CONTENTION and a logged victim, the counter and error-word bit 0
+    report it, every kernel returns, and the invariants still hold."""
+    f, b = 8, 4
+    base = workloads.keys(900 + m, 8 * m)
+    ks = np.concatenate([base] * 40 + [workloads.keys(901, 5000)])
+    g = cf.CuckooFilter(m, f, b, 50, eviction=eviction, victim_capacity=1 << 16)
+    g.set_cas_limit(1)
+    if slicing == "always":
+        g.set_slicing("always", 16)
+    o = oracle.OracleFilter(m, f, b, 50)
+    flags = g.insert(to_dev(ks)).cpu().numpy()
+    st = g.stats()
+    n_cont = int((flags == 2).sum())
+    assert n_cont > 0
+    assert st["contention"] == n_cont
+    assert st["error_word"] & 1
+    # With one attempt allowed, every failed CAS was a loop's first attempt
+    # (bin 0) and every loop that ran out had one: bins above 0 stay empty.
+    assert st["cas_retry"][0] >= n_cont and sum(st["cas_retry"][1:]) == 0
+    slots = slots_view(g.snapshot()[64:], m, f, b)
+    fp, i1, i2 = o.hash_batch(ks)
+    vt, vb = g.victims()
+    assert vt.size == st["victims"] == st["insert_fail"] == int((flags != 1).sum())
+    probs = check_insert(AltTable(o, fp), np.zeros_like(slots), slots, fp, i1, i2,
+                         vt, vb, 0)
+    assert probs == [], (probs, st)
+    assert st["occupancy"] == int(np.count_nonzero(slots))
+    # The default bound restored: a fresh batch on a fresh filter has none.
+    g.set_cas_limit(0)
+    g2 = cf.CuckooFilter(1 << 10, f, b, 50)
+    g2.insert(to_dev(workloads.keys(902, 3000)))
+    assert g2.stats()["contention"] == 0
+    with pytest.raises(Exception):
+        g.set_cas_limit(5000)
+
+
 def test_max_evictions_zero(cf):
     m, f, b = 1 << 6, 16, 4
     ks = workloads.keys(77, 2 * m * b)
@@ -363,6 +405,52 @@ def test_host_buffer_api_matches_device_api(cf):
     rf = g.remove_host(ks[:5000])
     assert rf.all()
     assert g.stats()["remove_ok"] == 5000
+
+
+@pytest.mark.parametrize("slicing", ["off", "always"])
+def test_async_host_calls_match_device_calls(cf, slicing):
+    """The asynchronous host-buffer calls, issued back to back without a
+    synchronisation in between (insert, query, delete, query), give what
+    the device calls give on the same table.  With slicing forced, passes of
+    5000 keys gather their keys in staging chunks of 1777, so every pass is
+    split across several chunks and the chunks across passes."""
+    m, f, b = 1 << 12, 16, 4
+    ks = workloads.keys(57, int(0.9 * m * b))
+    neg = workloads.keys(57, 9000, start=ks.size)
+    q = np.concatenate([ks, neg])
+    g = cf.CuckooFilter(m, f, b, 500)
+    g.set_staging_chunk(1777)
+    if slicing == "always":
+        g.set_slicing("always", 1024, 5000)
+    hk = torch.from_numpy(ks.view(np.int64)).pin_memory()
+    hq = torch.from_numpy(q.view(np.int64)).pin_memory()
+    fi = torch.empty(ks.size, dtype=torch.uint8).pin_memory()
+    fq = torch.empty(q.size, dtype=torch.uint8).pin_memory()
+    fd = torch.empty(4000, dtype=torch.uint8).pin_memory()
+    fq2 = torch.empty(q.size, dtype=torch.uint8).pin_memory()
+    st = torch.cuda.Stream()
+    g.insert_host_async(hk, out=fi, stream=st)
+    g.contains_host_async(hq, out=fq, stream=st)
+    g.remove_host_async(hk[:4000], out=fd, stream=st)
+    g.contains_host_async(hq, out=fq2, stream=st)
+    st.synchronize()
+    flags = fi.numpy()
+    # The inserts: the invariants on the table as it stood after them are
+    # checked through the first query (every key found) and the counters.
+    assert (flags == 1).all()
+    assert fq.numpy()[: ks.size].all()
+    assert fd.numpy().all()
+    # Device calls on the final table agree with the last async query.
+    dq = g.contains(to_dev(q)).cpu().numpy()
+    assert np.array_equal(fq2.numpy(), dq)
+    st_ = g.stats()
+    assert st_["insert_ok"] == ks.size and st_["remove_ok"] == 4000
+    assert st_["occupancy"] == ks.size - 4000 == g.count_occupied()
+    # The last query equals Alg. 2 evaluated by the oracle on the table the
+    # calls left.
+    ot = oracle.OracleFilter(m, f, b, 500)
+    ot.load(g.snapshot())
+    assert np.array_equal(ot.contains_batch(q), fq2.numpy())
 
 
 def test_create_at_caller_memory(cf):

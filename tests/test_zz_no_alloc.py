@@ -80,6 +80,83 @@ def test_noalloc_insert_matches_insert_on_two_calls():
         qa = ref.contains(to_dev(keys_so_far)).cpu().numpy()
         qb = nal.contains(to_dev(keys_so_far)).cpu().numpy()
         assert qa.all() and qb.all()
+    # At LF 0.88 some keys found both buckets full: the eviction loop ran
+    # on keys queued in the static array.
+    assert nal.stats()["evictions"] > 0
+
+
+def test_noalloc_full_static_queue_batch():
+    """A batch of exactly CF_NOALLOC_MAX_KEYS keys on a table pre-filled to
+    LF 0.45, ending at LF 0.95, so that a large share of the batch goes
+    through the static queue: the insert invariants hold against the
+    oracle's hashes, and the counters agree with the table."""
+    import paper_2603_15486_gb300 as cf
+    from paper_2603_15486_gb300 import _lib
+
+    L = _lib.load()
+    m, f, b = 1 << 19, 16, 4
+    nmax = 1 << 20
+    n0 = (m * b * 95) // 100 - nmax
+    nal = _filter_in_torch_memory(cf, m, f, b)
+    pre = workloads.keys(72, n0)
+    assert (nal.insert(to_dev(pre)).cpu().numpy() == 1).all()
+    st0 = nal.stats()
+    before = slots_view(nal.snapshot()[64:], m, f, b)
+    ks = workloads.keys(72, nmax, start=n0)
+    fl = torch.empty(nmax, dtype=torch.uint8, device="cuda")
+    rc = L.cf_insert_noalloc(nal.handle, to_dev(ks).data_ptr(), nmax, fl.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, L.cf_last_error()
+    fl = fl.cpu().numpy()
+    st = nal.stats()
+    o = oracle.OracleFilter(m, f, b, 500)
+    fp, i1, i2 = o.hash_batch(ks)
+    pfp, _, _ = o.hash_batch(pre)
+    alt = AltTable(o, np.concatenate([fp, pfp]))
+    after = slots_view(nal.snapshot()[64:], m, f, b)
+    vt, vb = nal.victims()
+    vt, vb = vt[st0["victims"]:], vb[st0["victims"]:]
+    assert check_insert(alt, before, after, fp, i1, i2, vt, vb, 0) == []
+    ev = st["evictions"] - st0["evictions"]
+    fails = st["insert_fail"] - st0["insert_fail"]
+    assert ev > nmax // 20            # many chains ran from the static queue
+    assert fails == int((fl != 1).sum()) == vt.size
+    assert st["occupancy"] == int(np.count_nonzero(after))
+    assert st["contention"] == 0 and st["error_word"] == 0
+
+
+def test_noalloc_two_filters_in_a_row_share_the_array():
+    """Two filters inserted into one after the other on one stream (the
+    ordering the shared array allows): each ends with exactly its own keys."""
+    import paper_2603_15486_gb300 as cf
+    from paper_2603_15486_gb300 import _lib
+
+    L = _lib.load()
+    stream = torch.cuda.current_stream()
+    geo = [(1 << 15, 16, 4, 73), (1 << 14, 8, 8, 74)]
+    filts, keysets, flags = [], [], []
+    for m, f, b, seed in geo:
+        filt = _filter_in_torch_memory(cf, m, f, b)
+        ks = workloads.keys(seed, int(0.95 * m * b))
+        fl = torch.empty(ks.size, dtype=torch.uint8, device="cuda")
+        rc = L.cf_insert_noalloc(filt.handle, to_dev(ks).data_ptr(), ks.size,
+                                 fl.data_ptr(), stream.cuda_stream)
+        assert rc == 0, L.cf_last_error()
+        filts.append(filt)
+        keysets.append(ks)
+        flags.append(fl)
+    torch.cuda.synchronize()
+    for (m, f, b, _), filt, ks, fl in zip(geo, filts, keysets, flags):
+        o = oracle.OracleFilter(m, f, b, 500)
+        fp, i1, i2 = o.hash_batch(ks)
+        alt = AltTable(o, fp)
+        after = slots_view(filt.snapshot()[64:], m, f, b)
+        vt, vb = filt.victims()
+        assert check_insert(alt, np.zeros_like(after), after, fp, i1, i2, vt, vb, 0) == []
+        st = filt.stats()
+        assert st["evictions"] > 0
+        assert st["insert_fail"] == int((fl.cpu().numpy() != 1).sum()) == vt.size
+        assert st["occupancy"] == int(np.count_nonzero(after))
 
 
 def test_noalloc_rejects_batches_beyond_the_static_scratch():
