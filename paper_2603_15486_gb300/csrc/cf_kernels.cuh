@@ -95,7 +95,7 @@ __device__ __forceinline__ void st_flag(uint8_t* p, uint8_t v) {
 // ---------------------------------------------------------------------------
 // One-word buckets (b*f <= 64): the loaded word is the whole bucket, so a
 // key's state is just its current word.
-template <class G, int K, bool INSERT>
+template <class G, int K, bool INSERT, bool RT = true>
 __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
                                             const uint32_t (&bkt)[K],
                                             const uint32_t (&tag)[K],
@@ -116,7 +116,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
     const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
     if (live[k] && !zero_lanes<G>(cur[k] ^ pat)) live[k] = false;
   }
-  for (uint32_t round = 0; round < cas_bound(d); ++round) {
+  for (uint32_t round = 0; round < cas_bound<RT>(d); ++round) {
     W old[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -152,7 +152,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
     if (live[k]) res[k] = TI_CONTENTION;
 }
 
-template <class G, int K, bool INSERT>
+template <class G, int K, bool INSERT, bool RT = true>
 __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
                                             const uint32_t (&bkt)[K],
                                             const uint32_t (&tag)[K],
@@ -186,7 +186,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
     }
     if (pos[k] == G::kWpb) live[k] = false;
   }
-  for (uint32_t round = 0; round < cas_bound(d); ++round) {
+  for (uint32_t round = 0; round < cas_bound<RT>(d); ++round) {
     W old[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -238,16 +238,16 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
     if (live[k]) res[k] = TI_CONTENTION;
 }
 
-template <class G, int K, bool INSERT>
+template <class G, int K, bool INSERT, bool RT = true>
 __device__ __forceinline__ void cas_many(const DevFilter& d,
                                          const uint32_t (&bkt)[K],
                                          const uint32_t (&tag)[K],
                                          const bool (&act)[K], int (&res)[K],
                                          uint32_t& first) {
   if constexpr (G::kWpb == 1)
-    cas_many_1w<G, K, INSERT>(d, bkt, tag, act, res, first);
+    cas_many_1w<G, K, INSERT, RT>(d, bkt, tag, act, res, first);
   else
-    cas_many_nw<G, K, INSERT>(d, bkt, tag, act, res, first);
+    cas_many_nw<G, K, INSERT, RT>(d, bkt, tag, act, res, first);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,7 +296,7 @@ struct QueuePush {
 // two buckets are both full go to the eviction queue; phase 2 runs them
 // separately so that the few long eviction chains do not hold whole warps
 // of finished keys.
-template <class G, int K, class Push>
+template <class G, int K, class Push, bool RT = true>
 __device__ __forceinline__ void tile_insert(const DevFilter& d,
                                             const uint64_t* __restrict__ keys,
                                             uint64_t n, uint64_t base,
@@ -315,7 +315,7 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
     bkt[k] = kh.i1;
     tag[k] = kh.fp;
   }
-  cas_many<G, K, true>(d, bkt, tag, valid, r1, c.cas_first);
+  cas_many<G, K, true, RT>(d, bkt, tag, valid, r1, c.cas_first);
   // Alternate buckets only for the keys whose primary bucket was full.
   bool act[K];
 #pragma unroll
@@ -326,7 +326,7 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
       tag[k] |= G::kChoice;
     }
   }
-  cas_many<G, K, true>(d, bkt, tag, act, r2, c.cas_first);
+  cas_many<G, K, true, RT>(d, bkt, tag, act, r2, c.cas_first);
   bool need[K];
   uint32_t qidx[K];
 #pragma unroll
@@ -395,7 +395,7 @@ __device__ __forceinline__ void tile_contains(const DevFilter& d,
 
 // Delete (Alg. 3): TryRemove(i1) or TryRemove(i2), the K keys' CASes
 // issued together.
-template <class G, int K>
+template <class G, int K, bool RT = true>
 __device__ __forceinline__ void tile_remove(const DevFilter& d,
                                             const uint64_t* __restrict__ keys,
                                             uint64_t n, uint64_t base,
@@ -413,7 +413,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
     bkt[k] = kh.i1;
     tag[k] = kh.fp;
   }
-  cas_many<G, K, false>(d, bkt, tag, valid, r1, c.cas_first);
+  cas_many<G, K, false, RT>(d, bkt, tag, valid, r1, c.cas_first);
   bool act[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -423,7 +423,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
       tag[k] |= G::kChoice;
     }
   }
-  cas_many<G, K, false>(d, bkt, tag, act, r2, c.cas_first);
+  cas_many<G, K, false, RT>(d, bkt, tag, act, r2, c.cas_first);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (!valid[k]) continue;
@@ -463,7 +463,7 @@ __device__ __forceinline__ int evict_one(const DevFilter& d, uint64_t key,
 // ---------------------------------------------------------------------------
 // Single-filter kernels: a persistent grid walks the batch's tiles.
 // ---------------------------------------------------------------------------
-template <class G, int K, int MINB = CF_MINB_MUT>
+template <class G, int K, int MINB = CF_MINB_MUT, bool RT = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
                 uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
@@ -474,7 +474,7 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
   TileCounts c;
   const QueuePush push{&d.ctrl->queue_count, queue};
   for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K))
-    tile_insert<G, K>(d, keys, n, base, lane, flags, evout, push, c);
+    tile_insert<G, K, QueuePush, RT>(d, keys, n, base, lane, flags, evout, push, c);
   block_add(&d.ctrl->occupancy, c.ok);
   block_add(&d.ctrl->insert_ok, c.ok);
   block_add(&d.ctrl->insert_fail, c.cont);
@@ -704,7 +704,7 @@ k_contains(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
     tile_contains<G, K>(d, keys, n, base, lane, flags);
 }
 
-template <class G, int K, int MINB = CF_MINB_MUT>
+template <class G, int K, int MINB = CF_MINB_MUT, bool RT = false>
 __global__ void __launch_bounds__(kBlock, MINB)
 k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
          uint8_t* __restrict__ flags) {
@@ -713,7 +713,7 @@ k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
   const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
   TileCounts c;
   for (uint64_t base = gw * (32u * K); base < n; base += nw * (32u * K))
-    tile_remove<G, K>(d, keys, n, base, lane, flags, c);
+    tile_remove<G, K, RT>(d, keys, n, base, lane, flags, c);
   block_add(&d.ctrl->occupancy, c.ok, /*negate=*/true);
   block_add(&d.ctrl->remove_ok, c.ok);
   block_add(&d.ctrl->remove_fail, c.fail + c.cont);
@@ -829,7 +829,9 @@ struct Launch {
   static cudaError_t remove(const DevFilter& d, const uint64_t* keys,
                             uint64_t n, uint8_t* flags, cudaStream_t s,
                             KernelTimer* t) {
-    auto fn = l2_table(d) ? k_remove<G, KM, MINB_L2> : k_remove<G, KM>;
+    auto fn = d.max_cas != kMaxCas ? k_remove<G, KM, CF_MINB_MUT, true>
+              : l2_table(d)        ? k_remove<G, KM, MINB_L2>
+                                   : k_remove<G, KM>;
     if (t) t->begin(KK_REMOVE, s);
     fn<<<persistent_grid(fn, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags);
     if (t) t->end(KK_REMOVE, s);
@@ -850,7 +852,9 @@ struct Launch {
                                   uint32_t n, uint8_t* flags, uint32_t* evout,
                                   uint32_t* queue, const EvictMap& em, cudaStream_t s,
                                   KernelTimer* t) {
-    auto f1 = l2_table(d) ? k_insert_direct<G, KM, MINB_L2> : k_insert_direct<G, KM>;
+    auto f1 = d.max_cas != kMaxCas ? k_insert_direct<G, KM, CF_MINB_MUT, true>
+              : l2_table(d)        ? k_insert_direct<G, KM, MINB_L2>
+                                   : k_insert_direct<G, KM>;
     if (t) t->begin(KK_INSERT_DIRECT, s);
     f1<<<persistent_grid(f1, n, kBlock * KM), kBlock, 0, s>>>(d, keys, n, flags,
                                                              evout, queue);

@@ -311,7 +311,7 @@ k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
 // 4*(S + 1) region lengths (T = kBlock*8 = 2048 records).
 // ---------------------------------------------------------------------------
 
-template <class G, int OP, int K>
+template <class G, int OP, int K, bool RT = false>
 __global__ void __launch_bounds__(kBlock, CF_SLICE_MINB)
 k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
   // R rounds of K records per thread: every tile holds 8 records per thread
@@ -428,7 +428,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
         for (int k = 0; k < K; ++k)
           res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
       } else {
-        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res, c.cas_first);
+        cas_many<G, K, OP == SOP_INSERT, RT>(d, bkt, tag, valid, res, c.cas_first);
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -506,7 +506,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
 // block tiles of kBlock*8 of those numbers are handed out in order by a
 // counter, so that only records are visited.
 // ---------------------------------------------------------------------------
-template <class G, int OP, int K>
+template <class G, int OP, int K, bool RT = false>
 __global__ void __launch_bounds__(kBlock, CF_SLICE2_MINB)
 k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
                uint32_t* __restrict__ queue) {
@@ -587,7 +587,7 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
           if (valid[k] && want_flags)
             st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
       } else {
-        cas_many<G, K, OP == SOP_INSERT>(d, bkt, tag, valid, res, c.cas_first);
+        cas_many<G, K, OP == SOP_INSERT, RT>(d, bkt, tag, valid, res, c.cas_first);
         bool to_queue[K];
         uint32_t qidx[K];
 #pragma unroll
@@ -771,7 +771,8 @@ struct SliceLaunch {
                             KernelTimer* t) {
     constexpr uint32_t T = kBlock * 8;
     const size_t smem = size_t(20) * T + size_t(24) * sb.n_slices + 16;
-    auto p1 = k_slice_probe1<G, OP, K>;
+    const bool rt = d.max_cas != kMaxCas;
+    auto p1 = rt ? k_slice_probe1<G, OP, K, true> : k_slice_probe1<G, OP, K>;
     cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(p1), smem);
     if (e != cudaSuccess) return e;
     if (t) t->begin(KK_SLICE_PROBE1, s);
@@ -779,7 +780,7 @@ struct SliceLaunch {
     if (t) t->end(KK_SLICE_PROBE1, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto p2 = k_slice_probe2<G, OP, K>;
+    auto p2 = rt ? k_slice_probe2<G, OP, K, true> : k_slice_probe2<G, OP, K>;
     const size_t smem2 = size_t(2) * (sb.n_slices + 1) * sizeof(uint32_t);
     if (t) t->begin(KK_SLICE_PROBE2, s);
     p2<<<persistent_grid(p2, n, kBlock * 8), kBlock, smem2, s>>>(d, sb, n, want, queue);
