@@ -106,7 +106,9 @@ typedef struct {
   uint64_t contention;     /* bounded CAS loops that ran out                */
   uint32_t error_word;     /* bit 0: contention; bit 1: victim log full;
                               bit 2: an asynchronous copy of the sliced
-                              path timed out (its records were skipped)    */
+                              path timed out (its records were skipped);
+                              bit 3: (bounds-checked build only) a bucket
+                              index was out of range, see debug_bad_index */
   uint32_t victim_capacity;
   uint64_t map_builds;     /* eviction launches that built and used the
                               full-bucket map (cf_set_eviction_map)        */
@@ -115,6 +117,9 @@ typedef struct {
                               2-3, 4-7, 8-15, 16-63, >= 64 (bin 0: a loop's
                               first attempt failed; bin k counts loops that
                               needed more retries than bins below k allow) */
+  uint64_t debug_bad_index;/* bounds-checked build: first out-of-range
+                              bucket index + 1; 0 if none (always 0 in the
+                              normal build, which does not check)          */
 } cf_stats_t;
 
 /* ---- sizes ------------------------------------------------------------- */
@@ -300,6 +305,19 @@ cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
  * the contention path (flags, counter, victim, error-word bit 0) without
  * any kernel waiting unboundedly.  Applies to calls made after it. */
 cf_status cf_debug_set_cas_limit(cf_filter* f, uint32_t limit);
+/* 1 if this build of the library range-checks every bucket index on the
+ * device (libcf_debug.so, built with -DCF_DEBUG_BOUNDS=1), else 0.  In a
+ * checked build an out-of-range index never reaches memory: bucket 0 is
+ * used instead, error-word bit 3 is set and the first such index is kept
+ * (cf_stats_t.debug_bad_index). */
+int cf_debug_bounds_checked(void);
+/* Test export: load bucket `bucket` on the device (through the same bucket
+ * addressing as the kernels) and return its number of occupied slots in
+ * *occupied (may be NULL).  Synchronous.  The normal build returns
+ * CF_EINVAL for bucket >= num_buckets; the checked build lets the kernel's
+ * own check catch it (the way to test that check). */
+cf_status cf_debug_touch_bucket(cf_filter* f, uint64_t bucket, uint64_t* occupied,
+                                void* stream);
 
 /* ---- multi-filter launch --------------------------------------------------
  * Many filters' insert / query / delete batches in ONE persistent kernel

@@ -10,7 +10,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcf.so")
+# CF_LIBRARY selects another build of the same library (the bounds-checked
+# libcf_debug.so that build.py --debug-bounds makes); default libcf.so.
+LIB_PATH = os.environ.get("CF_LIBRARY") or os.path.join(HERE, "libcf.so")
 
 
 class CfConfig(ctypes.Structure):
@@ -25,7 +27,8 @@ class CfStats(ctypes.Structure):
         "occupancy", "insert_ok", "insert_fail", "remove_ok", "remove_fail",
         "evictions", "victims", "rollbacks", "rollback_lost", "contention")] + [
         ("error_word", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32),
-        ("map_builds", ctypes.c_uint64), ("cas_retry", ctypes.c_uint64 * 7)]
+        ("map_builds", ctypes.c_uint64), ("cas_retry", ctypes.c_uint64 * 7),
+        ("debug_bad_index", ctypes.c_uint64)]
 
 
 class CfBatchItem(ctypes.Structure):
@@ -104,6 +107,8 @@ SIGNATURES = {
     "cf_set_slicing": (_st, [_vp, _int, _u64, _u64]),
     "cf_set_eviction_map": (_st, [_vp, _int, _u64]),
     "cf_debug_set_cas_limit": (_st, [_vp, _u32]),
+    "cf_debug_bounds_checked": (_int, []),
+    "cf_debug_touch_bucket": (_st, [_vp, _u64, ctypes.POINTER(_u64), _vp]),
     "cf_stats": (_st, [_vp, ctypes.POINTER(CfStats), _vp]),
     "cf_victims": (_st, [_vp, _vp, _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "cf_snapshot": (_st, [_vp, _vp, ctypes.c_size_t, _int, _vp]),

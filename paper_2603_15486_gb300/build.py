@@ -3,6 +3,10 @@
 Each .cu translation unit is compiled to an object in parallel, then linked
 into ``paper_2603_15486_gb300/libcf.so``.  Objects go to ``_build/`` beside
 this file; both are git-ignored.  Rebuilds only what changed.
+
+``build(debug_bounds=True)`` (``--debug-bounds``) makes the bounds-checked
+variant ``libcf_debug.so`` instead (every bucket index range-checked, see
+CF_DEBUG_BOUNDS in csrc/cf_device.cuh); load it with CF_LIBRARY=<path>.
 """
 from __future__ import annotations
 
@@ -19,6 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libcf.so")
+DEBUG_BUILD = BUILD + "-debug"
+DEBUG_LIB = os.path.join(HERE, "libcf_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -55,8 +61,8 @@ def _headers():
         os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _compile(src: str, extra=()):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra=(), build_dir: str = BUILD):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if (os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep
             and _elf_matches_host(obj)):
@@ -70,28 +76,32 @@ def _compile(src: str, extra=()):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False) -> str:
+    bdir = DEBUG_BUILD if debug_bounds else BUILD
+    lib = DEBUG_LIB if debug_bounds else LIB
+    extra = ("-DCF_DEBUG_BOUNDS=1",) if debug_bounds else ()
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     if force:
-        for o in glob.glob(os.path.join(BUILD, "*.o")):
+        for o in glob.glob(os.path.join(bdir, "*.o")):
             os.remove(o)
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(_compile, srcs))
+        objs = list(ex.map(lambda src: _compile(src, extra, bdir), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest
-            and _elf_matches_host(LIB)):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+    if (not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest
+            and _elf_matches_host(lib)):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}", file=sys.stderr)
-    return LIB
+        print(f"built {lib}", file=sys.stderr)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True,
+          debug_bounds="--debug-bounds" in sys.argv)

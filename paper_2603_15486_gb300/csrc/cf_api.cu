@@ -921,6 +921,7 @@ cf_status cf_stats(cf_filter* f, cf_stats_t* out, void* stream) {
   out->victim_capacity = f->d.victim_cap;
   out->map_builds = c.map_builds;
   for (int i = 0; i < 7; ++i) out->cas_retry[i] = c.cas_retry[i];
+  out->debug_bad_index = c.debug_bad_index;
   return mark(f, s);
 }
 
@@ -1050,6 +1051,32 @@ cf_status cf_hash_debug(const uint64_t* keys, uint64_t n, uint32_t fp_bits,
   }
   return CF_OK;
 }
+
+cf_status cf_debug_touch_bucket(cf_filter* f, uint64_t bucket, uint64_t* occupied,
+                                void* stream) {
+  if (!f) return CF_EINVAL;
+#if !CF_DEBUG_BOUNDS
+  // Without the kernels' own range check, an index beyond the table is
+  // refused here: the kernel would read outside the allocation.
+  if (bucket >= f->cfg.num_buckets) return CF_EINVAL;
+#endif
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cf_status st = order_on(f, s);
+  if (st != CF_OK) return st;
+  CF_CUDA(cudaMemsetAsync(&f->d.ctrl->scratch_count, 0, 8, s));
+  cudaError_t e = f->ops->touch(f->d, bucket, &f->d.ctrl->scratch_count, s);
+  if (e != cudaSuccess) {
+    set_err("touch kernel", e);
+    return CF_ECUDA;
+  }
+  unsigned long long v = 0;
+  CF_CUDA(cudaMemcpyAsync(&v, &f->d.ctrl->scratch_count, 8, cudaMemcpyDeviceToHost, s));
+  CF_CUDA(cudaStreamSynchronize(s));
+  if (occupied) *occupied = v;
+  return mark(f, s);
+}
+
+int cf_debug_bounds_checked(void) { return CF_DEBUG_BOUNDS; }
 
 cf_status cf_debug_insert_serial(cf_filter* f, const uint64_t* keys,
                                  uint64_t n, uint8_t* out_flags,

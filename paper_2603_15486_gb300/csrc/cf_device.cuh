@@ -409,10 +409,29 @@ __device__ __forceinline__ void note_cas_fail(const DevFilter& d, uint32_t r,
 // ---------------------------------------------------------------------------
 enum : int { TI_FULL = 0, TI_OK = 1, TI_CONTENTION = -1 };
 
+// Bounds-checked builds (-DCF_DEBUG_BOUNDS=1, the library's debug variant):
+// every bucket index is checked against m before its address is formed; a
+// bad one sets error-word bit 3, the first one is kept (index + 1) in the
+// control block, and bucket 0 is used instead, so the access stays inside
+// the table (the results are then wrong, and the error word says so).
+#ifndef CF_DEBUG_BOUNDS
+#define CF_DEBUG_BOUNDS 0
+#endif
+constexpr uint32_t kErrBounds = 8u;
+
+__device__ __forceinline__ uint64_t checked_bucket(const DevFilter& d, uint64_t j) {
+  if (CF_DEBUG_BOUNDS && j >= d.m) {
+    atomicOr(&d.ctrl->error_word, kErrBounds);
+    atomicCAS(&d.ctrl->debug_bad_index, 0ull, (unsigned long long)j + 1ull);
+    return 0;
+  }
+  return j;
+}
+
 template <class G>
 __device__ __forceinline__ typename G::Word* bucket_ptr(const DevFilter& d,
                                                         uint64_t j) {
-  return reinterpret_cast<typename G::Word*>(d.table) + j * G::kWpb;
+  return reinterpret_cast<typename G::Word*>(d.table) + checked_bucket(d, j) * G::kWpb;
 }
 
 // TryInsert (Alg. 1): start word (tag mod b) / tpw, wrap-around scan, CAS
@@ -674,10 +693,12 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
 // kept up by the eviction rounds (a round that fills a bucket, or finds a
 // bucket full that the map called open, sets its bit).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t map_word(const uint32_t* map, uint64_t j) {
-  return ld_cg_u32(map + (j >> 5));  // L2: coherent with the atomicOr below
+__device__ __forceinline__ uint32_t map_word(const DevFilter& d, const uint32_t* map,
+                                             uint64_t j) {
+  return ld_cg_u32(map + (checked_bucket(d, j) >> 5));  // L2: coherent with map_set
 }
-__device__ __forceinline__ void map_set(uint32_t* map, uint64_t j) {
+__device__ __forceinline__ void map_set(const DevFilter& d, uint32_t* map, uint64_t j) {
+  j = checked_bucket(d, j);
   atomicOr(map + (j >> 5), 1u << (j & 31));
 }
 
@@ -703,7 +724,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
   if (has_empty<G>(c.bk)) {
     // Only reachable under concurrency (a slot freed by a delete).
     if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first) == TI_OK) {
-      if (!has_empty<G>(c.bk)) map_set(map, c.cur);
+      if (!has_empty<G>(c.bk)) map_set(d, map, c.cur);
       return EV_OK;
     }
   }
@@ -717,7 +738,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
     cand[k] = t[k] != 0 && a[k] != c.cur;
   }
 #pragma unroll
-  for (int k = 0; k < H; ++k) mw[k] = cand[k] ? map_word(map, a[k]) : ~0u;
+  for (int k = 0; k < H; ++k) mw[k] = cand[k] ? map_word(d, map, a[k]) : ~0u;
   int chosen = H - 1;
   bool open = false;
 #pragma unroll
@@ -773,7 +794,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
   c.tag = moved;
   const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
   if (r == TI_OK) {
-    if (!has_empty<G>(c.bk)) map_set(map, c.cur);
+    if (!has_empty<G>(c.bk)) map_set(d, map, c.cur);
     return EV_OK;
   }
   if (r == TI_CONTENTION) {
@@ -784,7 +805,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
   }
   // c.cur is full.  Its bit is set already unless the map called it open
   // (stale) or the move went elsewhere than the chosen candidate's bucket.
-  if (open || !pre || evicted != tk) map_set(map, c.cur);
+  if (open || !pre || evicted != tk) map_set(d, map, c.cur);
   return ROUND_CONTINUE;
 }
 

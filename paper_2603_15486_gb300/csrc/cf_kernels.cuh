@@ -636,7 +636,7 @@ __device__ __forceinline__ int try_insert_mapped(const DevFilter& d, uint64_t j,
   Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
   uint32_t first = 0;  // one thread: no CAS ever fails
   const int r = try_insert_loaded<G>(d, j, tag, bk, first);
-  if (map && r == TI_OK && !has_empty<G>(bk)) map_set(map, j);
+  if (map && r == TI_OK && !has_empty<G>(bk)) map_set(d, map, j);
   return r;
 }
 
@@ -735,6 +735,23 @@ __global__ void k_hash(DevFilter d, const uint64_t* __restrict__ keys,
   }
 }
 
+// Test export: load bucket j through the (in bounds-checked builds,
+// checked) bucket address and add its nonzero slot count to *out.
+template <class G>
+__global__ void k_touch(DevFilter d, uint64_t j, unsigned long long* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
+  uint32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < G::kWpb; ++q) {
+    if constexpr (G::kW32)
+      c += G::kTpw - __popc(zero_lanes<G>(bk.w[q]));
+    else
+      c += G::kTpw - __popcll(zero_lanes<G>(bk.w[q]));
+  }
+  atomicAdd(out, (unsigned long long)c);
+}
+
 // Number of nonzero slots, added to *out.
 template <class G>
 __global__ void __launch_bounds__(kBlock)
@@ -773,12 +790,21 @@ inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
 // fit).  Its chains are bound by dependent random accesses, and more chains
 // in flight only add queueing (2^28-bucket workload, eviction ms per step
 // at 1 / 2 / 3 / 4 / 6 blocks per SM: 58.0 / 46.2 / 48.3 / 48.8 / 48.7).
+// With the full-bucket map a round loads one bucket from DRAM instead of
+// b/2, and the loop becomes bound by the latency of its dependent round
+// trips instead: more chains in flight pay (eviction ms per step at 2 / 3
+// / 4 blocks per SM: 39.4 / 36.7 / 37.9 with the map, 46.0 / 48.0 / 48.3
+// without), CF_EVICT_BPSM_MAP blocks per SM for launches that may use it.
 #ifndef CF_EVICT_BPSM
 #define CF_EVICT_BPSM 2
 #endif
-inline unsigned evict_grid(const void* fn) {
+#ifndef CF_EVICT_BPSM_MAP
+#define CF_EVICT_BPSM_MAP 3
+#endif
+inline unsigned evict_grid(const void* fn, bool map = false) {
   const int occ = cached_occupancy(fn, kBlock);
-  const int per = CF_EVICT_BPSM > 0 && CF_EVICT_BPSM < occ ? CF_EVICT_BPSM : occ;
+  const int want = map ? CF_EVICT_BPSM_MAP : CF_EVICT_BPSM;
+  const int per = want > 0 && want < occ ? want : occ;
   return unsigned(device_sm_count() * (per > 0 ? per : 1));
 }
 
@@ -865,7 +891,7 @@ struct Launch {
     if (e != cudaSuccess) return e;
     auto f2 = k_insert_evict<G>;
     if (t) t->begin(KK_INSERT_EVICT, s);
-    f2<<<evict_grid(reinterpret_cast<const void*>(f2)), kBlock, 0, s>>>(
+    f2<<<evict_grid(reinterpret_cast<const void*>(f2), em.bits != nullptr), kBlock, 0, s>>>(
         d, keys, flags, evout, queue, em.bits, em.min_q);
     if (t) t->end(KK_INSERT_EVICT, s);
     return cudaGetLastError();
@@ -886,6 +912,11 @@ struct Launch {
                           cudaStream_t s) {
     auto fn = k_hash<G>;
     fn<<<persistent_grid(fn, n, kBlock), kBlock, 0, s>>>(d, keys, n, fp, i1, i2);
+    return cudaGetLastError();
+  }
+  static cudaError_t touch(const DevFilter& d, uint64_t j, unsigned long long* out,
+                           cudaStream_t s) {
+    k_touch<G><<<1, 32, 0, s>>>(d, j, out);
     return cudaGetLastError();
   }
   static cudaError_t count(const DevFilter& d, unsigned long long* out,
@@ -921,6 +952,8 @@ struct Ops {
   cudaError_t (*sliced_finish)(const DevFilter&, int, uint64_t, uint8_t*,
                                const SliceBufs&, uint32_t*, const EvictMap&,
                                cudaStream_t, KernelTimer*);
+  // Test export: one bucket loaded through the kernels' addressing.
+  cudaError_t (*touch)(const DevFilter&, uint64_t, unsigned long long*, cudaStream_t);
 };
 
 // ops_for<G>() (the table of one geometry) is defined in cf_slice.cuh.

@@ -835,7 +835,7 @@ struct SliceLaunch {
       if (e != cudaSuccess) return e;
       auto fe = k_insert_evict<G, true>;
       if (t) t->begin(KK_INSERT_EVICT, s);
-      fe<<<evict_grid(reinterpret_cast<const void*>(fe)), kBlock, 0, s>>>(
+      fe<<<evict_grid(reinterpret_cast<const void*>(fe), em.bits != nullptr), kBlock, 0, s>>>(
           d, sb.rec2, want ? sb.f2 : nullptr, nullptr, queue, em.bits, em.min_q);
       if (t) t->end(KK_INSERT_EVICT, s);
       e = cudaGetLastError();
@@ -869,7 +869,8 @@ const Ops* ops_for() {
                         &Launch<G>::insert_chunk, &Launch<G>::insert_serial,
                         &Launch<G>::hash,         &Launch<G>::count,
                         &SliceLaunch<G>::run,     &SliceLaunch<G>::begin,
-                        &SliceLaunch<G>::scatter, &SliceLaunch<G>::finish};
+                        &SliceLaunch<G>::scatter, &SliceLaunch<G>::finish,
+                        &Launch<G>::touch};
   return &o;
 }
 

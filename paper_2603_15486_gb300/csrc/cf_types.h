@@ -30,7 +30,9 @@ struct Ctrl {
   // attempt): bins r = 0, 1, 2-3, 4-7, 8-15, 16-63, 64 and more.  Bin k thus
   // counts the loops that needed more than the retries of bins below it.
   unsigned long long cas_retry[7];
-  unsigned long long pad[11];
+  // Bounds-checked builds: the first out-of-range bucket index + 1 (0: none).
+  unsigned long long debug_bad_index;
+  unsigned long long pad[10];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
 
