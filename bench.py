@@ -1163,8 +1163,11 @@ def main(argv=None):
                     help="requests of the served-vs-plain summary trace")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-warmup", type=int, default=1)
-    ap.add_argument("--e2e-chunk", type=int, default=1 << 25,
-                    help="keys per staging chunk of the host-buffer calls")
+    ap.add_argument("--e2e-chunk", type=int, default=1 << 27,
+                    help="keys per staging chunk of the host-buffer calls (eight "
+                         "chunks are staged: 2^27 keys hold 8 GiB of keys in flight, "
+                         "enough to keep the host link busy through the longest "
+                         "eviction pass)")
     ap.add_argument("--slicing", choices=["off", "auto", "always"], default="auto",
                     help="slice-partitioned execution of the filter calls (cf_set_slicing)")
     ap.add_argument("--evict-map", choices=["off", "auto", "always"], default="auto",
