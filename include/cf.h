@@ -524,10 +524,12 @@ cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
  * (eviction loop, both paths), 2: contains, 3: remove; slice-partitioned
  * path (cf_set_slicing): 4: grouping by slice (counter reset, scatter),
  * 5: bucket-i1 pass, 6: bucket-i2 pass, 7: results back to key order;
- * 8: the full-bucket map of the eviction loop (cf_set_eviction_map).
+ * 8: the full-bucket map of the eviction loop (cf_set_eviction_map);
+ * the host-buffer calls' copies, timed on their own streams: 9: keys to the
+ * device (one record per staging chunk), 10: flags back to the host.
  * cf_read_kernel_times waits for the recorded events, sums their elapsed
  * times and (reset != 0) recycles them. */
-#define CF_KERNEL_KINDS 9
+#define CF_KERNEL_KINDS 11
 typedef struct {
   uint64_t launches[CF_KERNEL_KINDS];
   double ms[CF_KERNEL_KINDS];

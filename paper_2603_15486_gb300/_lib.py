@@ -70,7 +70,7 @@ class CfServerStats(ctypes.Structure):
 
 KERNEL_KINDS = ("insert_direct", "insert_evict", "contains", "remove",
                 "slice_split", "slice_probe1", "slice_probe2", "slice_merge",
-                "evict_map")
+                "evict_map", "copy_h2d", "copy_d2h")
 
 
 class CfKernelTimes(ctypes.Structure):

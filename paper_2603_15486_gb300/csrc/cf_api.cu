@@ -504,8 +504,10 @@ cf_status stage_keys(cf_filter* f, const uint64_t* keys_h, uint64_t len, cudaStr
   Stage& sg = f->stage[f->next_slot];
   f->next_slot = (f->next_slot + 1) % cfk::kStageSlots;
   if (sg.used) CF_CUDA(cudaStreamWaitEvent(f->s_in, sg.comp_done, 0));
+  if (f->timer) f->timer->begin(cfk::KK_H2D, f->s_in);
   CF_CUDA(cudaMemcpyAsync(sg.keys, keys_h, len * sizeof(uint64_t), cudaMemcpyHostToDevice,
                           f->s_in));
+  if (f->timer) f->timer->end(cfk::KK_H2D, f->s_in);
   CF_CUDA(cudaEventRecord(sg.in_done, f->s_in));
   CF_CUDA(cudaStreamWaitEvent(s, sg.in_done, 0));
   *out = &sg;
@@ -525,7 +527,9 @@ cf_status flush_group(cf_filter* f, cfk::FlagGroup* g, uint8_t* dst_h, uint64_t 
                       cudaStream_t s, cudaEvent_t* last_out) {
   CF_CUDA(cudaEventRecord(g->comp_done, s));
   CF_CUDA(cudaStreamWaitEvent(f->s_out, g->comp_done, 0));
+  if (f->timer) f->timer->begin(cfk::KK_D2H, f->s_out);
   CF_CUDA(cudaMemcpyAsync(dst_h, g->flags, bytes, cudaMemcpyDeviceToHost, f->s_out));
+  if (f->timer) f->timer->end(cfk::KK_D2H, f->s_out);
   CF_CUDA(cudaEventRecord(g->out_done, f->s_out));
   g->used = true;
   *last_out = g->out_done;

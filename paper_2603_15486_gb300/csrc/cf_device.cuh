@@ -618,11 +618,27 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   }
   c.ev++;
   if (evicted == 0) return EV_OK;
-  // Carry the evicted tag to its alternate bucket and insert it there.
-  uint32_t moved;
-  c.cur = alt_of<G>(d, c.cur, evicted, moved);
+  // Carry the evicted tag to its alternate bucket and insert it there.  The
+  // evicted tag is the chosen candidate's unless another thread changed the
+  // slot meanwhile; only then is its alternate bucket hashed again.
+  uint64_t an = 0;
+  uint32_t tk = 0, moved = 0;
+  bool pre = false;
+#pragma unroll
+  for (int k = 0; k < H; ++k)
+    if (k == chosen) {
+      an = a[k];
+      tk = t[k];
+      moved = mv[k];
+      pre = cand[k];
+    }
+  if (evicted == tk) {
+    c.cur = an;
+  } else {
+    c.cur = alt_of<G>(d, c.cur, evicted, moved);
+  }
   c.tag = moved;
-  if (cand[chosen] && evicted == t[chosen])
+  if (pre && evicted == tk)
     c.bk = tb;  // the probe's words of that very bucket
   else
     c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
@@ -693,13 +709,47 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
 // kept up by the eviction rounds (a round that fills a bucket, or finds a
 // bucket full that the map called open, sets its bit).
 // ---------------------------------------------------------------------------
+// The map's accesses carry an L2 evict_last policy (CF_MAP_EVICT_LAST): the
+// map is read by every round while the rounds' random bucket lines stream
+// through L2, and a map word evicted by them costs a round a second DRAM
+// access.
+#ifndef CF_MAP_EVICT_LAST
+#define CF_MAP_EVICT_LAST 1
+#endif
+__device__ __forceinline__ uint64_t map_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ uint32_t map_word(const DevFilter& d, const uint32_t* map,
                                              uint64_t j) {
-  return ld_cg_u32(map + (checked_bucket(d, j) >> 5));  // L2: coherent with map_set
+  const uint32_t* p = map + (checked_bucket(d, j) >> 5);
+  if (CF_MAP_EVICT_LAST) {
+    uint32_t v;
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;"
+                 : "=r"(v) : "l"(p), "l"(map_policy()));
+    return v;
+  }
+  return ld_cg_u32(p);  // L2: coherent with map_set
 }
 __device__ __forceinline__ void map_set(const DevFilter& d, uint32_t* map, uint64_t j) {
   j = checked_bucket(d, j);
-  atomicOr(map + (j >> 5), 1u << (j & 31));
+  uint32_t* p = map + (j >> 5);
+  const uint32_t bit = 1u << (j & 31);
+  if (CF_MAP_EVICT_LAST) {
+    uint32_t old;
+    asm volatile("atom.global.L2::cache_hint.or.b32 %0, [%1], %2, %3;"
+                 : "=r"(old) : "l"(p), "r"(bit), "l"(map_policy()) : "memory");
+  } else {
+    atomicOr(p, bit);
+  }
+}
+__device__ __forceinline__ void map_store(uint32_t* p, uint32_t v) {
+  if (CF_MAP_EVICT_LAST)
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;"
+                 :: "l"(p), "r"(v), "l"(map_policy()) : "memory");
+  else
+    *p = v;
 }
 
 // One round of the BFS eviction heuristic (Sec. 4.6.1) that asks the
@@ -748,14 +798,18 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
       chosen = k;
     }
   }
-  // The words of the bucket the evicted tag goes to, loaded while the swap's
-  // CAS runs.
+  // The chosen candidate's tag, its alternate bucket and the tag as stored
+  // there (computed above), and the words of that bucket, loaded while the
+  // swap's CAS runs.
   uint64_t an = 0;
+  uint32_t tk = 0, mvk = 0;
   bool pre = false;
 #pragma unroll
   for (int k = 0; k < H; ++k)
     if (k == chosen) {
       an = a[k];
+      tk = t[k];
+      mvk = mv[k];
       pre = cand[k];
     }
   Bucket<G> nb{};
@@ -783,12 +837,11 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
   }
   c.ev++;
   if (evicted == 0) return EV_OK;
-  uint32_t moved;
-  const uint64_t dest = alt_of<G>(d, c.cur, evicted, moved);
-  uint32_t tk = 0;
-#pragma unroll
-  for (int k = 0; k < H; ++k)
-    if (k == chosen) tk = t[k];
+  // The evicted tag is the chosen candidate's unless another thread changed
+  // the slot meanwhile; only then is its alternate bucket hashed again.
+  uint32_t moved = mvk;
+  uint64_t dest = an;
+  if (evicted != tk) dest = alt_of<G>(d, c.cur, evicted, moved);
   c.bk = (pre && evicted == tk) ? nb : load_bucket_ev<G>(bucket_ptr<G>(d, dest));
   c.cur = dest;
   c.tag = moved;
@@ -824,22 +877,35 @@ __device__ __forceinline__ Chain<G> chain_start(const DevFilter& d,
   return c;
 }
 
-// The bucket chain_start loads for this key.
+// The start of a chain without its bucket's words: the random stream after
+// the first draw, the bucket it picked (i1 or i2) and the tag as stored
+// there, from the key's 64-bit hash.  The alternate bucket is hashed only
+// when the draw picks it.
 template <class G>
-__device__ __forceinline__ uint64_t chain_first_bucket(const KeyHash& kh) {
-  uint64_t rng = kh.h;
-  return (rng_next(rng) & 1) == 0 ? kh.i1 : kh.i2;
+struct ChainHead {
+  uint64_t rng;
+  uint64_t cur;
+  uint32_t tag;
+};
+template <class G>
+__device__ __forceinline__ ChainHead<G> chain_head(const DevFilter& d, uint64_t h) {
+  const KeyHash kh = hash_from_h<G>(d, h);
+  ChainHead<G> p;
+  p.rng = h;
+  const bool first = (rng_next(p.rng) & 1) == 0;
+  p.cur = first ? kh.i1 : alt_index<G>(d, kh.i1, kh.fp);
+  p.tag = first ? kh.fp : (kh.fp | G::kChoice);
+  return p;
 }
 
-// chain_start with that bucket's words loaded beforehand.
+// chain_start from a head whose bucket's words were loaded beforehand.
 template <class G>
-__device__ __forceinline__ Chain<G> chain_start_loaded(const KeyHash& kh,
+__device__ __forceinline__ Chain<G> chain_start_loaded(const ChainHead<G>& p,
                                                        const Bucket<G>& bk) {
   Chain<G> c;
-  c.rng = kh.h;
-  const bool first = (rng_next(c.rng) & 1) == 0;
-  c.cur = first ? kh.i1 : kh.i2;
-  c.tag = first ? kh.fp : (kh.fp | G::kChoice);
+  c.rng = p.rng;
+  c.cur = p.cur;
+  c.tag = p.tag;
   c.ev = 0;
   c.bk = bk;
   return c;

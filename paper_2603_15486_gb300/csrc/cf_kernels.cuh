@@ -523,16 +523,17 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
   uint32_t idx = 0;
   bool active = false;
   // The lane's next chain: stage 0 none, 1 queue entry pidx loading, 2 key
-  // pkey loading, 3 its first bucket pbk loading.
+  // pkey loading, 3 its head pch computed and its first bucket pbk loading
+  // (the head is computed once: its hashes serve the chain's start).
   uint32_t pst = 0, pidx = 0;
   uint64_t pkey = 0;
+  ChainHead<G> pch{};
   Bucket<G> pbk{};
-  auto key_hash = [&](uint64_t k) {
-    return FROM_HASH ? hash_full_from_h<G>(d, k) : hash_key<G>(d, k);
-  };
+  auto key_h = [&](uint64_t k) { return FROM_HASH ? k : xxh64_u64(k); };
   for (;;) {
     if (CF_EVICT_PREP && pst == 2 && d.max_ev != 0) {
-      pbk = load_bucket_ev<G>(bucket_ptr<G>(d, chain_first_bucket<G>(key_hash(pkey))));
+      pch = chain_head<G>(d, key_h(pkey));
+      pbk = load_bucket_ev<G>(bucket_ptr<G>(d, pch.cur));
       pst = 3;
     } else if (CF_EVICT_PREP && pst == 1) {
       pkey = keys[pidx];
@@ -555,14 +556,18 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
       const bool pst3 = pst == 3;
       idx = pidx;
       pst = 0;
-      const KeyHash kh = key_hash(pkey);
       if (d.max_ev == 0) {
+        const KeyHash kh = hash_from_h<G>(d, key_h(pkey));
         log_victim(d, kh.fp, kh.i1);
         if (flags) st_flag(flags + idx, EV_FAIL);
         if (evout) evout[idx] = 0;
         n_fail++;
       } else {
-        c = pst3 ? chain_start_loaded<G>(kh, pbk) : chain_start<G>(d, kh);
+        if (!pst3) {
+          pch = chain_head<G>(d, key_h(pkey));
+          pbk = load_bucket_ev<G>(bucket_ptr<G>(d, pch.cur));
+        }
+        c = chain_start_loaded<G>(pch, pbk);
         active = true;
       }
     }
@@ -625,7 +630,7 @@ k_fullmap(DevFilter d, uint32_t* __restrict__ map, uint32_t min_q) {
     bool full = false;
     if (j < d.m) full = !has_empty<G>(load_bucket<G, true>(bucket_ptr<G>(d, j)));
     const unsigned bits = __ballot_sync(0xFFFFFFFFu, full);
-    if (lane == 0) map[g] = bits;
+    if (lane == 0) map_store(map + g, bits);
   }
 }
 
@@ -820,7 +825,9 @@ enum KernelKind : int {
   KK_SLICE_PROBE2 = 6,  // ... bucket i2 pass
   KK_SLICE_MERGE = 7,   // ... merge + out (results back to key order)
   KK_EVICT_MAP = 8,     // full-bucket map of the eviction loop
-  KK_NUM = 9
+  KK_H2D = 9,           // host-buffer calls: key copies to the device
+  KK_D2H = 10,          // ... flag copies back to the host
+  KK_NUM = 11
 };
 
 // The full-bucket map of one insert call: bits (m/32 words, rounded up) or
