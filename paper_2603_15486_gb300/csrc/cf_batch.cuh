@@ -88,6 +88,18 @@ __device__ __forceinline__ void warp_add(unsigned long long* dst, uint32_t v,
   if (lane == 0 && s) atomicAdd(dst, negate ? (0ull - s) : (unsigned long long)s);
 }
 
+// A warp's CAS counts added to the histogram (every lane must call it).
+__device__ __forceinline__ void cas_count_warp_add(const DevFilter& d, const CasCount& cc,
+                                                   uint32_t lane) {
+  if (!CF_CAS_HIST) return;
+  warp_add(&d.ctrl->cas_retry[0], cc.first, lane);
+  if (__any_sync(0xFFFFFFFFu, cc.deep != 0)) {
+#pragma unroll
+    for (int bin = 1; bin <= 6; ++bin)
+      warp_add(&d.ctrl->cas_retry[bin], (cc.deep >> (5 * (bin - 1))) & 31u, lane);
+  }
+}
+
 template <class G, int K, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 k_batch_tiles(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
@@ -116,14 +128,14 @@ k_batch_tiles(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
       warp_add(&d.ctrl->insert_ok, c.ok, lane);
       warp_add(&d.ctrl->insert_fail, c.cont, lane);
       warp_add(&d.ctrl->contention, c.cont, lane);
-      warp_add(&d.ctrl->cas_retry[0], c.cas_first, lane);
+      cas_count_warp_add(d, c.cas, lane);
     } else {
       tile_remove<G, K>(d, I.keys, I.n, base, lane, I.flags, c);
       warp_add(&d.ctrl->occupancy, c.ok, lane, /*negate=*/true);
       warp_add(&d.ctrl->remove_ok, c.ok, lane);
       warp_add(&d.ctrl->remove_fail, c.fail + c.cont, lane);
       warp_add(&d.ctrl->contention, c.cont, lane);
-      warp_add(&d.ctrl->cas_retry[0], c.cas_first, lane);
+      cas_count_warp_add(d, c.cas, lane);
     }
   }
 }
@@ -180,7 +192,7 @@ k_batch_evict(BatchCtl* ctl, const BatchItemDev* __restrict__ items,
         atomicAdd(&d.ctrl->contention, (unsigned long long)ec.contention);
         atomicOr(&d.ctrl->error_word, 1u);
       }
-      if (ec.cas_first) atomicAdd(&d.ctrl->cas_retry[0], (unsigned long long)ec.cas_first);
+      if (ec.cas.first | ec.cas.deep) cas_count_add(d, ec.cas);
       if (r != ROUND_CONTINUE) {
         if (r != EV_OK) log_victim(d, vt, vb);
         if (I.flags) st_flag(I.flags + q.y, uint8_t(r));

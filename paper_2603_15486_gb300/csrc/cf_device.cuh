@@ -33,8 +33,8 @@ __device__ __forceinline__ uint32_t cas_bound(const DevFilter& d) {
   return RT ? d.max_cas : kMaxCas;
 }
 
-// CF_CAS_HIST=0 builds without the CAS-retry histogram (about 1 ms per
-// step of the large workload).
+// CF_CAS_HIST=0 builds without the CAS-retry histogram (0.5 ms of the
+// 106 ms step of the large workload).
 #ifndef CF_CAS_HIST
 #define CF_CAS_HIST 1
 #endif
@@ -388,19 +388,49 @@ __device__ __forceinline__ uint64_t rng_next(uint64_t& s) {
 }
 
 // A failed CAS at retry depth r (0: the loop's first attempt) goes into the
-// filter's CAS-retry histogram.  First attempts fail often where many keys
-// meet in few buckets (the slice-grouped passes), so they are counted in
-// the thread (`first`, added to the histogram once per block or warp by
-// the kernel); deeper retries are rare and go to the histogram directly.
-__device__ __forceinline__ void note_cas_fail(const DevFilter& d, uint32_t r,
-                                              uint32_t& first) {
+// filter's CAS-retry histogram.  Failures are frequent wherever many keys
+// meet in few buckets (the slice-grouped passes, small tables), so every bin
+// is counted in the thread: the first-attempt bin in a word, the deeper bins
+// (1, 2-3, 4-7, 8-15, 16-63, >= 64) as 5-bit fields of another word, each
+// field added to the histogram when it would pass 30 and at the kernel's end.
+// Only the failure path pays.
+struct CasCount {
+  uint32_t first = 0;  // bin 0
+  uint32_t deep = 0;   // bins 1..6, 5 bits each
+};
+// n failed CAS attempts at retry depth r.  The multi-key loops tally a
+// round's failures and call this once per round, so the bin arithmetic is
+// not repeated for every key of the unrolled loop.  n <= 30.
+__device__ __forceinline__ void note_cas_fails(const DevFilter& d, uint32_t r, uint32_t n,
+                                               CasCount& cc) {
   if (!CF_CAS_HIST) return;
   if (r == 0) {
-    ++first;
+    cc.first += n;
     return;
   }
   const int bin = r == 1 ? 1 : r < 4 ? 2 : r < 8 ? 3 : r < 16 ? 4 : r < 64 ? 5 : 6;
-  atomicAdd(&d.ctrl->cas_retry[bin], 1ull);
+  const int sh = 5 * (bin - 1);
+  const uint32_t v = ((cc.deep >> sh) & 31u) + n;
+  if (v > 30u) {
+    atomicAdd(&d.ctrl->cas_retry[bin], (unsigned long long)v);
+    cc.deep &= ~(31u << sh);
+  } else {
+    cc.deep += n << sh;
+  }
+}
+__device__ __forceinline__ void note_cas_fail(const DevFilter& d, uint32_t r,
+                                              CasCount& cc) {
+  note_cas_fails(d, r, 1u, cc);
+}
+// The thread's counts, added by one thread (single-thread kernels and the
+// per-round flush of the multi-filter eviction kernel).
+__device__ __forceinline__ void cas_count_add(const DevFilter& d, CasCount& cc) {
+  if (cc.first) atomicAdd(&d.ctrl->cas_retry[0], (unsigned long long)cc.first);
+  for (int bin = 1; cc.deep && bin <= 6; ++bin) {
+    const uint32_t v = (cc.deep >> (5 * (bin - 1))) & 31u;
+    if (v) atomicAdd(&d.ctrl->cas_retry[bin], (unsigned long long)v);
+  }
+  cc = CasCount{};
 }
 
 // ---------------------------------------------------------------------------
@@ -441,7 +471,7 @@ __device__ __forceinline__ typename G::Word* bucket_ptr(const DevFilter& d,
 // observed, so the caller can keep using it without another load.
 template <class G>
 __device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
-                                 Bucket<G>& bk, uint32_t& first) {
+                                 Bucket<G>& bk, CasCount& first) {
   using W = typename G::Word;
   W* base = bucket_ptr<G>(d, j);
   const int start = int((tag % G::B) / G::kTpw);
@@ -470,7 +500,7 @@ __device__ int try_insert_loaded(const DevFilter& d, uint64_t j, uint32_t tag,
 
 template <class G>
 __device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag,
-                          uint32_t& first) {
+                          CasCount& first) {
   Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
   return try_insert_loaded<G>(d, j, tag, bk, first);
 }
@@ -478,7 +508,7 @@ __device__ int try_insert(const DevFilter& d, uint64_t j, uint32_t tag,
 // TryRemove (Alg. 3): same scan order; CAS the lowest matching lane to 0.
 template <class G>
 __device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag,
-                          uint32_t& first) {
+                          CasCount& first) {
   using W = typename G::Word;
   W* base = bucket_ptr<G>(d, j);
   const Bucket<G> bk = load_bucket<G, false>(base);
@@ -505,7 +535,7 @@ __device__ int try_remove(const DevFilter& d, uint64_t j, uint32_t tag,
 
 struct EvictCounters {
   uint32_t rollbacks = 0, rollback_lost = 0, contention = 0;
-  uint32_t cas_first = 0;  // failed first CAS attempts (note_cas_fail)
+  CasCount cas;  // failed CAS attempts by retry depth (note_cas_fail)
 };
 
 // Result codes of the eviction loops (the key's flag).
@@ -561,7 +591,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   W* cbase = bucket_ptr<G>(d, c.cur);
   if (has_empty<G>(c.bk)) {
     // Only reachable under concurrency (a slot freed by a delete).
-    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first) == TI_OK) return EV_OK;
+    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas) == TI_OK) return EV_OK;
   }
   uint32_t t[H], mv[H];
   uint64_t a[H];
@@ -607,7 +637,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
       swapped = true;
       break;
     }
-    note_cas_fail(d, tries, ec.cas_first);
+    note_cas_fail(d, tries, ec.cas);
     w = old;
   }
   if (!swapped) {
@@ -642,7 +672,7 @@ __device__ int bfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
     c.bk = tb;  // the probe's words of that very bucket
   else
     c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
-  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas);
   if (r == TI_OK) return EV_OK;
   if (r == TI_CONTENTION) {
     ec.contention++;
@@ -674,7 +704,7 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
       swapped = true;
       break;
     }
-    note_cas_fail(d, tries, ec.cas_first);
+    note_cas_fail(d, tries, ec.cas);
     w = old;
   }
   if (!swapped) {
@@ -689,7 +719,7 @@ __device__ int dfs_round(const DevFilter& d, Chain<G>& c, uint32_t& vt,
   c.cur = alt_of<G>(d, c.cur, evicted, moved);
   c.tag = moved;
   c.bk = load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
-  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas);
   if (r == TI_OK) return EV_OK;
   if (r == TI_CONTENTION) {
     ec.contention++;
@@ -773,7 +803,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
   W* cbase = bucket_ptr<G>(d, c.cur);
   if (has_empty<G>(c.bk)) {
     // Only reachable under concurrency (a slot freed by a delete).
-    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first) == TI_OK) {
+    if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas) == TI_OK) {
       if (!has_empty<G>(c.bk)) map_set(d, map, c.cur);
       return EV_OK;
     }
@@ -826,7 +856,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
       swapped = true;
       break;
     }
-    note_cas_fail(d, tries, ec.cas_first);
+    note_cas_fail(d, tries, ec.cas);
     w = old;
   }
   if (!swapped) {
@@ -845,7 +875,7 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
   c.bk = (pre && evicted == tk) ? nb : load_bucket_ev<G>(bucket_ptr<G>(d, dest));
   c.cur = dest;
   c.tag = moved;
-  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas_first);
+  const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas);
   if (r == TI_OK) {
     if (!has_empty<G>(c.bk)) map_set(d, map, c.cur);
     return EV_OK;
@@ -1011,6 +1041,18 @@ __device__ __forceinline__ void block_add(unsigned long long* dst, uint32_t v,
     if (lane == 0 && y) atomicAdd(dst, negate ? (0ull - y) : y);
   }
   __syncthreads();
+}
+
+// The block's CAS counts added to the histogram (every thread of the block
+// must call it; the deep bins cost barriers only when some thread has them).
+__device__ __forceinline__ void cas_count_block_add(const DevFilter& d, const CasCount& cc) {
+  if (!CF_CAS_HIST) return;
+  block_add(&d.ctrl->cas_retry[0], cc.first);
+  if (__syncthreads_or(cc.deep != 0)) {
+#pragma unroll
+    for (int bin = 1; bin <= 6; ++bin)
+      block_add(&d.ctrl->cas_retry[bin], (cc.deep >> (5 * (bin - 1))) & 31u);
+  }
 }
 
 }  // namespace cfk

@@ -100,7 +100,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
                                             const uint32_t (&bkt)[K],
                                             const uint32_t (&tag)[K],
                                             const bool (&act)[K],
-                                            int (&res)[K], uint32_t& first) {
+                                            int (&res)[K], CasCount& first) {
   using W = typename G::Word;
   W cur[K];
   bool live[K];
@@ -128,6 +128,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
       old[k] = atomicCAS(bucket_ptr<G>(d, bkt[k]), cur[k], desired);
     }
     bool any = false;
+    uint32_t nf = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!live[k]) continue;
@@ -136,7 +137,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
         live[k] = false;
         continue;
       }
-      note_cas_fail(d, round, first);
+      ++nf;
       cur[k] = old[k];
       const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
       if (!zero_lanes<G>(cur[k] ^ pat)) {
@@ -145,6 +146,7 @@ __device__ __forceinline__ void cas_many_1w(const DevFilter& d,
       }
       any = true;
     }
+    if (nf) note_cas_fails(d, round, nf, first);
     if (!any) break;
   }
 #pragma unroll
@@ -157,7 +159,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
                                             const uint32_t (&bkt)[K],
                                             const uint32_t (&tag)[K],
                                             const bool (&act)[K], int (&res)[K],
-                                            uint32_t& first) {
+                                            CasCount& first) {
   using W = typename G::Word;
   Bucket<G> bk[K];
   W cur[K];
@@ -199,6 +201,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
       old[k] = atomicCAS(p, cur[k], desired);
     }
     bool any = false;
+    uint32_t nf = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!live[k]) continue;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
         live[k] = false;
         continue;
       }
-      note_cas_fail(d, round, first);
+      ++nf;
       cur[k] = old[k];
       const W pat = INSERT ? W(0) : broadcast<G>(tag[k]);
       if (!zero_lanes<G>(cur[k] ^ pat)) {
@@ -231,6 +234,7 @@ __device__ __forceinline__ void cas_many_nw(const DevFilter& d,
       }
       any = true;
     }
+    if (nf) note_cas_fails(d, round, nf, first);
     if (!any) break;
   }
 #pragma unroll
@@ -243,7 +247,8 @@ __device__ __forceinline__ void cas_many(const DevFilter& d,
                                          const uint32_t (&bkt)[K],
                                          const uint32_t (&tag)[K],
                                          const bool (&act)[K], int (&res)[K],
-                                         uint32_t& first) {
+                                         CasCount& first) {
+  static_assert(K <= 30, "a round's failure tally must fit a histogram field");
   if constexpr (G::kWpb == 1)
     cas_many_1w<G, K, INSERT, RT>(d, bkt, tag, act, res, first);
   else
@@ -259,7 +264,7 @@ __device__ __forceinline__ void cas_many(const DevFilter& d,
 // ---------------------------------------------------------------------------
 struct TileCounts {
   uint32_t ok = 0, fail = 0, cont = 0;
-  uint32_t cas_first = 0;  // failed first CAS attempts (note_cas_fail)
+  CasCount cas;  // failed CAS attempts by retry depth (note_cas_fail)
 };
 
 // Appends key indices to a filter's eviction queue: the K keys of every
@@ -315,7 +320,7 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
     bkt[k] = kh.i1;
     tag[k] = kh.fp;
   }
-  cas_many<G, K, true, RT>(d, bkt, tag, valid, r1, c.cas_first);
+  cas_many<G, K, true, RT>(d, bkt, tag, valid, r1, c.cas);
   // Alternate buckets only for the keys whose primary bucket was full.
   bool act[K];
 #pragma unroll
@@ -326,7 +331,7 @@ __device__ __forceinline__ void tile_insert(const DevFilter& d,
       tag[k] |= G::kChoice;
     }
   }
-  cas_many<G, K, true, RT>(d, bkt, tag, act, r2, c.cas_first);
+  cas_many<G, K, true, RT>(d, bkt, tag, act, r2, c.cas);
   bool need[K];
   uint32_t qidx[K];
 #pragma unroll
@@ -413,7 +418,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
     bkt[k] = kh.i1;
     tag[k] = kh.fp;
   }
-  cas_many<G, K, false, RT>(d, bkt, tag, valid, r1, c.cas_first);
+  cas_many<G, K, false, RT>(d, bkt, tag, valid, r1, c.cas);
   bool act[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -423,7 +428,7 @@ __device__ __forceinline__ void tile_remove(const DevFilter& d,
       tag[k] |= G::kChoice;
     }
   }
-  cas_many<G, K, false, RT>(d, bkt, tag, act, r2, c.cas_first);
+  cas_many<G, K, false, RT>(d, bkt, tag, act, r2, c.cas);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (!valid[k]) continue;
@@ -479,7 +484,7 @@ k_insert_direct(DevFilter d, const uint64_t* __restrict__ keys, uint32_t n,
   block_add(&d.ctrl->insert_ok, c.ok);
   block_add(&d.ctrl->insert_fail, c.cont);
   block_add(&d.ctrl->contention, c.cont);
-  block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  cas_count_block_add(d, c.cas);
   if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 
@@ -597,7 +602,7 @@ k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
   block_add(&d.ctrl->rollbacks, ec.rollbacks);
   block_add(&d.ctrl->rollback_lost, ec.rollback_lost);
   block_add(&d.ctrl->contention, ec.contention);
-  block_add(&d.ctrl->cas_retry[0], ec.cas_first);
+  cas_count_block_add(d, ec.cas);
   if (ec.contention) atomicOr(&d.ctrl->error_word, 1u);
   if (threadIdx.x == 0) {
     __threadfence();
@@ -639,7 +644,7 @@ template <class G>
 __device__ __forceinline__ int try_insert_mapped(const DevFilter& d, uint64_t j,
                                                  uint32_t tag, uint32_t* map) {
   Bucket<G> bk = load_bucket<G, false>(bucket_ptr<G>(d, j));
-  uint32_t first = 0;  // one thread: no CAS ever fails
+  CasCount first;  // one thread: no CAS ever fails
   const int r = try_insert_loaded<G>(d, j, tag, bk, first);
   if (map && r == TI_OK && !has_empty<G>(bk)) map_set(d, map, j);
   return r;
@@ -723,7 +728,7 @@ k_remove(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
   block_add(&d.ctrl->remove_ok, c.ok);
   block_add(&d.ctrl->remove_fail, c.fail + c.cont);
   block_add(&d.ctrl->contention, c.cont);
-  block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  cas_count_block_add(d, c.cas);
   if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 

@@ -428,7 +428,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
         for (int k = 0; k < K; ++k)
           res[k] = valid[k] && bucket_has<G>(bk[k], tag[k]) ? TI_OK : TI_FULL;
       } else {
-        cas_many<G, K, OP == SOP_INSERT, RT>(d, bkt, tag, valid, res, c.cas_first);
+        cas_many<G, K, OP == SOP_INSERT, RT>(d, bkt, tag, valid, res, c.cas);
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -495,7 +495,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
     block_add(&d.ctrl->remove_fail, c.cont);
     block_add(&d.ctrl->contention, c.cont);
   }
-  if constexpr (OP != SOP_CONTAINS) block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  if constexpr (OP != SOP_CONTAINS) cas_count_block_add(d, c.cas);
   if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 
@@ -587,7 +587,7 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
           if (valid[k] && want_flags)
             st_flag(sb.f2 + q[k], bucket_has<G>(bk[k], tag[k]) ? 1 : 0);
       } else {
-        cas_many<G, K, OP == SOP_INSERT, RT>(d, bkt, tag, valid, res, c.cas_first);
+        cas_many<G, K, OP == SOP_INSERT, RT>(d, bkt, tag, valid, res, c.cas);
         bool to_queue[K];
         uint32_t qidx[K];
 #pragma unroll
@@ -626,7 +626,7 @@ k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
     block_add(&d.ctrl->remove_fail, c.fail + c.cont);
     block_add(&d.ctrl->contention, c.cont);
   }
-  if constexpr (OP != SOP_CONTAINS) block_add(&d.ctrl->cas_retry[0], c.cas_first);
+  if constexpr (OP != SOP_CONTAINS) cas_count_block_add(d, c.cas);
   if (c.cont) atomicOr(&d.ctrl->error_word, 1u);
 }
 

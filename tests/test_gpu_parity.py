@@ -302,6 +302,12 @@ def test_contention_stress_tiny_tables(cf, m, eviction):
     assert st["occupancy"] == int(np.count_nonzero(slots))
     assert st["insert_fail"] == int((flags != 1).sum()) == st["victims"]
     assert st["occupancy"] <= m * b
+    # CAS-retry histogram: forty copies of every key race for a few buckets,
+    # so first attempts fail; a loop that failed at depth r failed at every
+    # depth below it, so bin 0 >= bin 1, and bin 2 (depths 2-3) <= 2 x bin 1.
+    h = st["cas_retry"]
+    assert h[0] > 0 and h[0] >= h[1] and h[2] <= 2 * h[1]
+    assert all(x >= 0 for x in h)
 
 
 @pytest.mark.parametrize("m", [1 << 4, 1 << 6])
