@@ -36,6 +36,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "insert/query/delete Mops/s at LF 0.95 vs HBM roofline; served p99 vs plain"
+# Eviction levels per insert pass when --levels is 0 (the library default).
+DEFAULT_LEVELS = 12
 
 # DRAM bytes (read + write) per launch of the dominant kernel come from the
 # committed ncu summary of the large workload, which records them with a
@@ -306,6 +308,7 @@ def gpu_arm(args):
     filt = CuckooFilter(W.m, W.f, W.b, W.max_evictions)
     filt.set_slicing(args.slicing, args.slice_bytes, args.slice_chunk)
     filt.set_eviction_map(args.evict_map)
+    filt.set_eviction_levels(args.evict_levels, args.levels)
     stream.synchronize()
 
     segs = W.insert_segments()
@@ -396,6 +399,7 @@ def gpu_arm(args):
                    "parallelism": f"replicas x{ws}",
                    "slicing": args.slicing, "slice_chunk": args.slice_chunk or (1 << 28),
                    "evict_map": args.evict_map,
+                   "evict_levels": args.evict_levels,
                    "slice_bytes": args.slice_bytes or (32 << 20),
                    "l2": "no flush: 2 GiB table and 8 GB key arrays exceed the 129 MB L2"},
         "phases": {k: {"ms": round(v * 1e3, 3),
@@ -405,14 +409,20 @@ def gpu_arm(args):
                                    ("delete", med["delete"], W.n_deletes))},
         # Kernels launched in the timed steps, from the per-kernel timer (one
         # timer record covers merge + out).
-        "gpu_launches": sum(n_l * {"slice_merge": 2}.get(k, 1)
+        # The levels' record covers the seed and the levels.
+        "gpu_launches": sum(n_l * {"slice_merge": 2,
+                                   "evict_level": (args.levels or DEFAULT_LEVELS) + 1}.get(k, 1)
                             for k, (n_l, _) in ktimes.items()),
         "checks": {"insert_ok": ins_ok, "insert_fail": W.n_insert - ins_ok,
                    "query_pos_found": q_pos, "query_pos": W.n_queries // 2,
                    "false_positives": q_neg, "fpr": q_neg / (W.n_queries // 2),
                    "occupancy_after_step": st_end["occupancy"],
                    "evictions_per_step": st["evictions"],
-                   "contention": st_end["contention"]},
+                   "contention": st_end["contention"],
+                   "eviction_levels_per_step": st_end["level_passes"],
+                   "level_steps_per_step": st_end["level_steps"],
+                   "level_runout_per_step": st_end["level_runout"],
+                   "cas_retry_per_step": st_end["cas_retry"]},
         "clocks": clocks,
     }
 
@@ -435,6 +445,18 @@ def gpu_arm(args):
     # (the counters restart with every step's clear, so st_end holds one
     # step's builds).
     kb["evict_map"] = st_end["map_builds"] * (W.table_bytes + (W.m + 31) // 32 * 4)
+    # The eviction (Alg. 1 phase 2) of a sliced insert runs as the slice-
+    # grouped levels and the loop for the queues they leave: one entry
+    # ("eviction", the loop's launches) with the eviction's algorithmic bytes.
+    ktimes = dict(ktimes)
+    lv = ktimes.pop("evict_level", (0, 0.0))
+    evict_parts = None
+    if lv[0]:
+        le, mse = ktimes.pop("insert_evict", (0, 0.0))
+        ktimes["eviction"] = (lv[0], mse + lv[1])
+        kb["eviction"] = kb["insert_evict"]
+        evict_parts = {"levels_ms_per_step": round(lv[1] / args.steps, 3),
+                       "loop_and_rest_ms_per_step": round(mse / args.steps, 3)}
     peak = peaks.get("hbm_gbs") or 6800.0
     kern = {}
     for k, (launches, ms) in ktimes.items():
@@ -446,6 +468,8 @@ def gpu_arm(args):
                    ("stream_bytes_per_step" if k.startswith("slice") or k == "evict_map"
                     else "algorithmic_bytes_per_step"): int(kb[k]),
                    "achieved_GBps": round(ach, 1), "frac": round(ach / peak, 4)}
+        if k == "eviction" and evict_parts:
+            kern[k].update(evict_parts)
     # Per operation: the method's algorithmic bytes (32 B per bucket sector
     # the oracle touches + 9 B) at the measured operation rate.
     bpo = bytes_per_op(phases, W.f * W.b // 8)
@@ -1217,6 +1241,10 @@ def main(argv=None):
                     help="slice-partitioned execution of the filter calls (cf_set_slicing)")
     ap.add_argument("--evict-map", choices=["off", "auto", "always"], default="auto",
                     help="full-bucket map of the eviction loop (cf_set_eviction_map)")
+    ap.add_argument("--evict-levels", choices=["off", "on"], default="on",
+                    help="slice-grouped eviction levels (cf_set_eviction_levels)")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="eviction levels per insert pass (0: the library default, 12)")
     ap.add_argument("--slice-bytes", type=int, default=0,
                     help="table bytes per slice (0: the library default, 32 MiB)")
     ap.add_argument("--slice-chunk", type=int, default=0,

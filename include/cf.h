@@ -120,6 +120,11 @@ typedef struct {
   uint64_t debug_bad_index;/* bounds-checked build: first out-of-range
                               bucket index + 1; 0 if none (always 0 in the
                               normal build, which does not check)          */
+  uint64_t level_passes;   /* slice-grouped eviction levels that ran
+                              (cf_set_eviction_levels)                     */
+  uint64_t level_steps;    /* chain steps those levels took                */
+  uint64_t level_runout;   /* chains run to their end at once for want of
+                              room in a level's record buffer             */
 } cf_stats_t;
 
 /* ---- sizes ------------------------------------------------------------- */
@@ -261,6 +266,30 @@ cf_status cf_set_slicing(cf_filter* f, int mode, uint64_t slice_bytes,
  *  - cf_debug_insert_serial uses (and keeps exact) the map in mode 2.
  * CF_EINVAL for a bad mode.  Takes effect with the next insert call. */
 cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue);
+
+/* Slice-grouped eviction levels of the sliced insert (Alg. 1 phase 2 with
+ * the BFS heuristic of Sec. 4.6.1, run level by level).  Instead of walking
+ * each key's eviction chain to its end (a random DRAM access per round on a
+ * table L2 cannot hold), every chain advances one step per level and a
+ * level's steps are grouped by the table slice of the bucket they touch, as
+ * the bucket passes group keys, so they hit L2.  A step: place the tag in
+ * hand into its bucket if it has an empty slot; else give up after
+ * max_evictions overwrites; else choose a candidate as the BFS heuristic
+ * does (asking the full-bucket map) and swap the tag in.  Each chain takes
+ * the same steps and random draws as in the eviction loop; only the
+ * interleaving of chains changes.
+ * Used for sliced inserts (cf_set_slicing) of BFS filters when the
+ * full-bucket map is (cf_set_eviction_map), for passes whose eviction queue
+ * holds at least min_queue keys (0: 2^20) and at most half the pass; after
+ * n_levels levels (0: 12), or once a level would have fewer than stop_queue
+ * chains (0: 2^18), the remaining chains run to their end as in the loop.
+ * The library allocates two record buffers of about 12 bytes per key of a
+ * pass each on first use (freed by cf_destroy, or here when n_levels
+ * changes).  mode: 0 off, 1 on (the default).  CF_EINVAL for a bad mode or
+ * n_levels > 256.  Waits for the filter's queued work; takes effect with
+ * the next insert call. */
+cf_status cf_set_eviction_levels(cf_filter* f, int mode, uint32_t n_levels,
+                                 uint64_t min_queue, uint64_t stop_queue);
 
 /* ---- state, stats, snapshots (synchronous) ------------------------------ */
 /* Counters of the filter (Sec. 4.3: the occupancy count kept by the
@@ -526,10 +555,14 @@ cf_status cf_insert_noalloc(cf_filter* f, const uint64_t* keys, uint64_t n,
  * 5: bucket-i1 pass, 6: bucket-i2 pass, 7: results back to key order;
  * 8: the full-bucket map of the eviction loop (cf_set_eviction_map);
  * the host-buffer calls' copies, timed on their own streams: 9: keys to the
- * device (one record per staging chunk), 10: flags back to the host.
+ * device (one record per staging chunk), 10: flags back to the host;
+ * 11: the slice-grouped eviction levels of a sliced insert (the seed and
+ * the levels; cf_set_eviction_levels), whose remaining chains run to their
+ * end under kind 1 (which then also holds the loop's launch for a queue the
+ * levels left alone).
  * cf_read_kernel_times waits for the recorded events, sums their elapsed
  * times and (reset != 0) recycles them. */
-#define CF_KERNEL_KINDS 11
+#define CF_KERNEL_KINDS 12
 typedef struct {
   uint64_t launches[CF_KERNEL_KINDS];
   double ms[CF_KERNEL_KINDS];

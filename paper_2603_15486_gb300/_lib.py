@@ -28,7 +28,9 @@ class CfStats(ctypes.Structure):
         "evictions", "victims", "rollbacks", "rollback_lost", "contention")] + [
         ("error_word", ctypes.c_uint32), ("victim_capacity", ctypes.c_uint32),
         ("map_builds", ctypes.c_uint64), ("cas_retry", ctypes.c_uint64 * 7),
-        ("debug_bad_index", ctypes.c_uint64)]
+        ("debug_bad_index", ctypes.c_uint64),
+        ("level_passes", ctypes.c_uint64), ("level_steps", ctypes.c_uint64),
+        ("level_runout", ctypes.c_uint64)]
 
 
 class CfBatchItem(ctypes.Structure):
@@ -70,7 +72,7 @@ class CfServerStats(ctypes.Structure):
 
 KERNEL_KINDS = ("insert_direct", "insert_evict", "contains", "remove",
                 "slice_split", "slice_probe1", "slice_probe2", "slice_merge",
-                "evict_map", "copy_h2d", "copy_d2h")
+                "evict_map", "copy_h2d", "copy_d2h", "evict_level")
 
 
 class CfKernelTimes(ctypes.Structure):
@@ -106,6 +108,7 @@ SIGNATURES = {
     "cf_set_staging_chunk": (_st, [_vp, _u64]),
     "cf_set_slicing": (_st, [_vp, _int, _u64, _u64]),
     "cf_set_eviction_map": (_st, [_vp, _int, _u64]),
+    "cf_set_eviction_levels": (_st, [_vp, _int, ctypes.c_uint32, _u64, _u64]),
     "cf_debug_set_cas_limit": (_st, [_vp, _u32]),
     "cf_debug_bounds_checked": (_int, []),
     "cf_debug_touch_bucket": (_st, [_vp, _u64, ctypes.POINTER(_u64), _vp]),

@@ -344,14 +344,88 @@ cf_status ensure_map(cf_filter* f) {
   return CF_OK;
 }
 
-// The map argument of one insert call (allocating the map on first use).
-cf_status evict_map_for(cf_filter* f, cfk::EvictMap* em) {
+// Slice-grouped eviction levels (cf_levels.cuh), for sliced BFS inserts
+// with the full-bucket map.  Defaults: 12 levels; the levels run for
+// eviction queues of at least 2^20 keys, and stop once a level would have
+// fewer than 2^18 chains (the rest run to their end in the loop's manner).
+// The record buffers hold half a pass (two buffers of 24 bytes per record,
+// about 26 bytes per key of the pass); a larger queue takes the eviction
+// loop.
+constexpr uint32_t kLevelsDefault = 12;
+constexpr uint32_t kLevelsMax = 256;
+constexpr uint64_t kLevelMinQueue = 1ull << 20;
+constexpr uint64_t kLevelStopQueue = 1ull << 18;
+
+uint32_t clamp_u32(uint64_t v) { return uint32_t(v < 0xFFFFFFFFull ? v : 0xFFFFFFFFull); }
+
+void free_levels(cf_filter* f) {
+  if (f->lv_mem) cudaFree(f->lv_mem);
+  f->lv_mem = nullptr;
+  f->lv = cfk::LevelBufs{};
+  f->lv_cap_n = 0;
+}
+
+// Buffers for passes of up to n keys over the slice geometry of f->sb.
+cf_status ensure_levels(cf_filter* f, uint64_t n) {
+  const uint32_t S = f->sb.n_slices;
+  const uint32_t L = f->lv_levels ? f->lv_levels : kLevelsDefault;
+  if (f->lv_mem && f->lv_cap_n >= n && f->lv.n_levels == L &&
+      f->lv.fill && f->lv.cap && f->lv_slices == S)
+    return CF_OK;
+  free_levels(f);
+  const uint64_t R = (n + 1) / 2;
+  const double per = double(R) / S;
+  const uint64_t cap = uint64_t(per + 6.0 * sqrt(per)) + 64;
+  const uint64_t spill = R / 16 + 1024;
+  const uint64_t recs = uint64_t(S) * cap + spill;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  // Counters and ctl adjacent: one memset clears both.
+  const size_t fill_bytes = size_t(L + 1) * (S + 2) * 128;
+  const size_t o_fill = take(fill_bytes + size_t(L + 2) * 4);
+  const size_t o_r0 = take(recs * 24), o_r1 = take(recs * 24);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_err, sizeof g_err, "eviction level buffers of %llu bytes",
+             (unsigned long long)off);
+    return CF_ENOMEM;
+  }
+  cfk::LevelBufs& lb = f->lv;
+  lb.fill = reinterpret_cast<uint32_t*>(mem + o_fill);
+  lb.ctl = reinterpret_cast<uint32_t*>(mem + o_fill + fill_bytes);
+  lb.rec[0] = reinterpret_cast<uint64_t*>(mem + o_r0);
+  lb.rec[1] = reinterpret_cast<uint64_t*>(mem + o_r1);
+  lb.cap = cap;
+  lb.spill = spill;
+  lb.n_levels = L;
+  f->lv_mem = mem;
+  f->lv_cap_n = n;
+  f->lv_slices = S;
+  return CF_OK;
+}
+
+// The map argument of one insert call (allocating the map on first use);
+// with level_n > 0 (a sliced pass of up to level_n keys) also the eviction
+// levels.
+cf_status evict_map_for(cf_filter* f, cfk::EvictMap* em, uint64_t level_n = 0) {
   *em = cfk::EvictMap{};
   if (!use_map(f)) return CF_OK;
   cf_status st = ensure_map(f);
   if (st != CF_OK) return st;
   em->bits = f->fullmap;
   em->min_q = map_min_queue(f);
+  if (level_n && f->lv_mode == 1) {
+    st = ensure_levels(f, level_n);
+    if (st != CF_OK) return st;
+    em->lv = f->lv;
+    em->lv.min_q = clamp_u32(f->lv_min_queue ? f->lv_min_queue : kLevelMinQueue);
+    em->lv.stop_q = clamp_u32(f->lv_stop_queue ? f->lv_stop_queue : kLevelStopQueue);
+  }
   return CF_OK;
 }
 
@@ -429,7 +503,7 @@ cf_status run_sliced(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
   if (op == OP_INSERT) {
     st = ensure_queue(f, chunk, kSliceChunkMax);
     if (st != CF_OK) return st;
-    st = evict_map_for(f, &em);
+    st = evict_map_for(f, &em, chunk);
     if (st != CF_OK) return st;
   }
   for (uint64_t off = 0; off < n; off += chunk) {
@@ -551,7 +625,7 @@ cf_status host_sliced(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
   if (op == OP_INSERT) {
     st = ensure_queue(f, plen, kSliceChunkMax);
     if (st != CF_OK) return st;
-    st = evict_map_for(f, &em);
+    st = evict_map_for(f, &em, plen);
     if (st != CF_OK) return st;
   }
   if (flags_h) {
@@ -719,6 +793,19 @@ cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue) {
   return CF_OK;
 }
 
+cf_status cf_set_eviction_levels(cf_filter* f, int mode, uint32_t n_levels,
+                                 uint64_t min_queue, uint64_t stop_queue) {
+  if (!f || mode < 0 || mode > 1 || n_levels > kLevelsMax) return CF_EINVAL;
+  // Buffers in use by queued work are freed only after that work.
+  if (f->has_last) CF_CUDA(cudaEventSynchronize(f->ext_ev ? f->ext_ev : f->last_ev));
+  if (n_levels != f->lv_levels) free_levels(f);
+  f->lv_mode = mode;
+  f->lv_levels = n_levels;
+  f->lv_min_queue = min_queue;
+  f->lv_stop_queue = stop_queue;
+  return CF_OK;
+}
+
 cf_status cf_debug_set_cas_limit(cf_filter* f, uint32_t limit) {
   if (!f || limit > cfk::kMaxCas) return CF_EINVAL;
   f->d.max_cas = limit ? limit : cfk::kMaxCas;
@@ -814,6 +901,7 @@ cf_status cf_destroy(cf_filter* f) {
   free_staging(f);
   if (f->queue) cudaFree(f->queue);
   if (f->fullmap) cudaFree(f->fullmap);
+  free_levels(f);
   free_slice(f);
   if (f->last_ev) cudaEventDestroy(f->last_ev);
   delete f->timer;
@@ -926,6 +1014,9 @@ cf_status cf_stats(cf_filter* f, cf_stats_t* out, void* stream) {
   out->map_builds = c.map_builds;
   for (int i = 0; i < 7; ++i) out->cas_retry[i] = c.cas_retry[i];
   out->debug_bad_index = c.debug_bad_index;
+  out->level_passes = c.level_passes;
+  out->level_steps = c.level_steps;
+  out->level_runout = c.level_runout;
   return mark(f, s);
 }
 

@@ -782,6 +782,115 @@ __device__ __forceinline__ void map_store(uint32_t* p, uint32_t v) {
     *p = v;
 }
 
+// The tag as stored in the alternate bucket of a bucket that holds t (the
+// `moved` of alt_of: the Offset policy flips the choice bit).
+template <class G>
+__device__ __forceinline__ uint32_t moved_tag(uint32_t t) {
+  return G::POLICY == 0 ? t : (t ^ G::kChoice);
+}
+
+// The CAS loop of a swap: c.tag into lane `lane` of word wi of bucket c.cur,
+// from the word as last seen (w), attempts tries0 .. the bound.  True with
+// the lane's previous tag in evicted; false if the bound ran out.
+template <class G>
+__device__ __forceinline__ bool swap_cas(const DevFilter& d, const Chain<G>& c, int wi, int lane,
+                                         typename G::Word w, uint32_t tries0, CasCount& cc,
+                                         uint32_t& evicted) {
+  using W = typename G::Word;
+  W* p = bucket_ptr<G>(d, c.cur) + wi;
+  for (uint32_t tries = tries0; tries < cas_bound(d); ++tries) {
+    const W old = atomicCAS(p, w, replace_lane<G>(w, lane, c.tag));
+    if (old == w) {
+      evicted = get_lane<G>(w, lane);
+      return true;
+    }
+    note_cas_fail(d, tries, cc);
+    w = old;
+  }
+  return false;
+}
+
+// After a swap took `evicted` from the chosen slot (whose tag was tk when
+// the candidates were read; its alternate bucket an, a candidate when pre,
+// open if the map called an open): EV_OK if the slot was empty, else
+// ROUND_CONTINUE with c at the evicted tag's alternate bucket and tag as
+// stored there, and mark = whether that bucket's map bit may be clear (the
+// map called it open, or the move went elsewhere than the chosen
+// candidate's bucket).  The evicted tag is tk unless another thread changed
+// the slot meanwhile; only then is its alternate bucket hashed again.
+template <class G>
+__device__ __forceinline__ int swap_tail(const DevFilter& d, Chain<G>& c, uint32_t evicted,
+                                         uint32_t tk, uint64_t an, bool pre, bool open,
+                                         bool& mark) {
+  c.ev++;
+  if (evicted == 0) return EV_OK;
+  uint32_t moved = moved_tag<G>(tk);
+  uint64_t dest = an;
+  if (evicted != tk) dest = alt_of<G>(d, c.cur, evicted, moved);
+  mark = open || !pre || evicted != tk;
+  c.cur = dest;
+  c.tag = moved;
+  return ROUND_CONTINUE;
+}
+
+// The choice and the swap of a BFS round with the full-bucket map, for the
+// tag c.tag destined for the full bucket c.cur (words c.bk), with the
+// round's random start.  Returns EV_OK (the swap took an empty slot),
+// EV_CONTENTION (vt/vb = the tag dropped and its bucket) or ROUND_CONTINUE
+// (see swap_tail).  With PREFETCH the chosen candidate's alternate bucket is
+// loaded while the swap's CAS runs: nb holds its words when have_nb.
+template <class G, bool PREFETCH>
+__device__ __forceinline__ int bfs_swap_map(const DevFilter& d, Chain<G>& c, uint32_t start,
+                                            uint32_t* map, uint32_t& vt, uint64_t& vb,
+                                            EvictCounters& ec, bool& mark, Bucket<G>& nb,
+                                            bool& have_nb) {
+  constexpr int H = G::B / 2;
+  uint32_t t[H], mw[H];
+  uint64_t a[H];
+  bool cand[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    t[k] = get_slot<G>(c.bk, (start + k) & (G::B - 1));
+    uint32_t mv;
+    a[k] = alt_of<G>(d, c.cur, t[k], mv);
+    cand[k] = t[k] != 0 && a[k] != c.cur;
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) mw[k] = cand[k] ? map_word(d, map, a[k]) : ~0u;
+  int chosen = H - 1;
+  bool open = false;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    if (!open && cand[k] && !((mw[k] >> (a[k] & 31)) & 1u)) {
+      open = true;
+      chosen = k;
+    }
+  }
+  // The chosen candidate's tag and alternate bucket (computed above).
+  uint64_t an = 0;
+  uint32_t tk = 0;
+  bool pre = false;
+#pragma unroll
+  for (int k = 0; k < H; ++k)
+    if (k == chosen) {
+      an = a[k];
+      tk = t[k];
+      pre = cand[k];
+    }
+  if (PREFETCH && pre) nb = load_bucket_ev<G>(bucket_ptr<G>(d, an));
+  const uint32_t sl = (start + uint32_t(chosen)) & (G::B - 1);
+  const int wi = int(sl / G::kTpw), lane = int(sl % G::kTpw);
+  uint32_t evicted = 0;
+  if (!swap_cas<G>(d, c, wi, lane, select_word<G>(c.bk, wi), 0, ec.cas, evicted)) {
+    ec.contention++;
+    vt = c.tag;
+    vb = c.cur;
+    return EV_CONTENTION;
+  }
+  have_nb = PREFETCH && pre && evicted == tk;
+  return swap_tail<G>(d, c, evicted, tk, an, pre, open, mark);
+}
+
 // One round of the BFS eviction heuristic (Sec. 4.6.1) that asks the
 // full-bucket map, not the buckets themselves, whether each candidate's
 // alternate bucket has an empty slot.  Same candidates, same choice (the
@@ -797,10 +906,7 @@ __device__ __forceinline__ void map_store(uint32_t* p, uint32_t v) {
 template <class G>
 __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
                              uint32_t& vt, uint64_t& vb, EvictCounters& ec) {
-  using W = typename G::Word;
-  constexpr int H = G::B / 2;
   const uint32_t start = uint32_t(rng_next(c.rng) & (G::B - 1));
-  W* cbase = bucket_ptr<G>(d, c.cur);
   if (has_empty<G>(c.bk)) {
     // Only reachable under concurrency (a slot freed by a delete).
     if (try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas) == TI_OK) {
@@ -808,73 +914,11 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
       return EV_OK;
     }
   }
-  uint32_t t[H], mv[H], mw[H];
-  uint64_t a[H];
-  bool cand[H];
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    t[k] = get_slot<G>(c.bk, (start + k) & (G::B - 1));
-    a[k] = alt_of<G>(d, c.cur, t[k], mv[k]);
-    cand[k] = t[k] != 0 && a[k] != c.cur;
-  }
-#pragma unroll
-  for (int k = 0; k < H; ++k) mw[k] = cand[k] ? map_word(d, map, a[k]) : ~0u;
-  int chosen = H - 1;
-  bool open = false;
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    if (!open && cand[k] && !((mw[k] >> (a[k] & 31)) & 1u)) {
-      open = true;
-      chosen = k;
-    }
-  }
-  // The chosen candidate's tag, its alternate bucket and the tag as stored
-  // there (computed above), and the words of that bucket, loaded while the
-  // swap's CAS runs.
-  uint64_t an = 0;
-  uint32_t tk = 0, mvk = 0;
-  bool pre = false;
-#pragma unroll
-  for (int k = 0; k < H; ++k)
-    if (k == chosen) {
-      an = a[k];
-      tk = t[k];
-      mvk = mv[k];
-      pre = cand[k];
-    }
+  bool mark = false, have_nb = false;
   Bucket<G> nb{};
-  if (pre) nb = load_bucket_ev<G>(bucket_ptr<G>(d, an));
-  const uint32_t sl = (start + uint32_t(chosen)) & (G::B - 1);
-  const int wi = int(sl / G::kTpw), lane = int(sl % G::kTpw);
-  W w = select_word<G>(c.bk, wi);
-  bool swapped = false;
-  uint32_t evicted = 0;
-  for (uint32_t tries = 0; tries < cas_bound(d); ++tries) {
-    const W old = atomicCAS(cbase + wi, w, replace_lane<G>(w, lane, c.tag));
-    if (old == w) {
-      evicted = get_lane<G>(w, lane);
-      swapped = true;
-      break;
-    }
-    note_cas_fail(d, tries, ec.cas);
-    w = old;
-  }
-  if (!swapped) {
-    ec.contention++;
-    vt = c.tag;
-    vb = c.cur;
-    return EV_CONTENTION;
-  }
-  c.ev++;
-  if (evicted == 0) return EV_OK;
-  // The evicted tag is the chosen candidate's unless another thread changed
-  // the slot meanwhile; only then is its alternate bucket hashed again.
-  uint32_t moved = mvk;
-  uint64_t dest = an;
-  if (evicted != tk) dest = alt_of<G>(d, c.cur, evicted, moved);
-  c.bk = (pre && evicted == tk) ? nb : load_bucket_ev<G>(bucket_ptr<G>(d, dest));
-  c.cur = dest;
-  c.tag = moved;
+  const int sw = bfs_swap_map<G, true>(d, c, start, map, vt, vb, ec, mark, nb, have_nb);
+  if (sw != ROUND_CONTINUE) return sw;
+  c.bk = have_nb ? nb : load_bucket_ev<G>(bucket_ptr<G>(d, c.cur));
   const int r = try_insert_loaded<G>(d, c.cur, c.tag, c.bk, ec.cas);
   if (r == TI_OK) {
     if (!has_empty<G>(c.bk)) map_set(d, map, c.cur);
@@ -886,9 +930,8 @@ __device__ int bfs_round_map(const DevFilter& d, Chain<G>& c, uint32_t* map,
     vb = c.cur;
     return EV_CONTENTION;
   }
-  // c.cur is full.  Its bit is set already unless the map called it open
-  // (stale) or the move went elsewhere than the chosen candidate's bucket.
-  if (open || !pre || evicted != tk) map_set(d, map, c.cur);
+  // c.cur is full.  Its bit is set already unless the swap marked it.
+  if (mark) map_set(d, map, c.cur);
   return ROUND_CONTINUE;
 }
 

@@ -1,6 +1,6 @@
 // Kernel instantiations for 32-bit fingerprints (b in {4, 8, 16}, XOR and
 // Offset bucket policies).
-#include "cf_slice.cuh"
+#include "cf_launch.cuh"
 
 namespace cfk {
 

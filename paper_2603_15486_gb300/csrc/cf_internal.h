@@ -132,5 +132,15 @@ struct cf_filter {
   int map_mode = 1;                    // 0 off, 1 automatic, 2 always
   uint64_t map_min_queue = 0;          // 0: automatic rule
   uint32_t* fullmap = nullptr;
+  // Slice-grouped eviction levels (cf_set_eviction_levels): mode, levels,
+  // thresholds (0: defaults) and the record buffers (allocated on first use).
+  int lv_mode = 1;                     // 0 off, 1 on (sliced BFS inserts with the map)
+  uint32_t lv_levels = 0;
+  uint64_t lv_min_queue = 0;
+  uint64_t lv_stop_queue = 0;
+  cfk::LevelBufs lv{};
+  uint64_t lv_cap_n = 0;               // keys per pass the buffers are sized for
+  uint32_t lv_slices = 0;              // slices they are laid out for
+  void* lv_mem = nullptr;
 };
 

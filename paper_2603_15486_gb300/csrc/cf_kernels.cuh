@@ -514,8 +514,13 @@ template <class G, bool FROM_HASH = false>
 __global__ void __launch_bounds__(kBlock, CF_MINB_EVICT)
 k_insert_evict(DevFilter d, const uint64_t* __restrict__ keys,
                uint8_t* __restrict__ flags, uint32_t* __restrict__ evout,
-               const uint32_t* __restrict__ queue, uint32_t* map, uint32_t min_q) {
-  const uint32_t qn = *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
+               const uint32_t* __restrict__ queue, uint32_t* map, uint32_t min_q,
+               const uint32_t* levels_on) {
+  // levels_on: nonzero when the slice-grouped eviction levels took this
+  // queue (cf_levels.cuh); the kernel then only resets the queue.
+  const uint32_t qn = levels_on && __ldcg(levels_on)
+                          ? 0u
+                          : *reinterpret_cast<volatile unsigned int*>(&d.ctrl->queue_count);
   const bool use_map = map != nullptr && qn >= min_q && d.eviction == 0;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -832,7 +837,8 @@ enum KernelKind : int {
   KK_EVICT_MAP = 8,     // full-bucket map of the eviction loop
   KK_H2D = 9,           // host-buffer calls: key copies to the device
   KK_D2H = 10,          // ... flag copies back to the host
-  KK_NUM = 11
+  KK_EVICT_LEVEL = 11,  // slice-grouped eviction levels (seed + levels)
+  KK_NUM = 12
 };
 
 // The full-bucket map of one insert call: bits (m/32 words, rounded up) or
@@ -840,6 +846,9 @@ enum KernelKind : int {
 struct EvictMap {
   uint32_t* bits = nullptr;
   uint32_t min_q = 0;
+  // The slice-grouped eviction levels (sliced passes only; lv.rec[0] null:
+  // none).
+  LevelBufs lv{};
 };
 struct KernelTimer {
   virtual void begin(int kind, cudaStream_t s) = 0;
@@ -904,7 +913,7 @@ struct Launch {
     auto f2 = k_insert_evict<G>;
     if (t) t->begin(KK_INSERT_EVICT, s);
     f2<<<evict_grid(reinterpret_cast<const void*>(f2), em.bits != nullptr), kBlock, 0, s>>>(
-        d, keys, flags, evout, queue, em.bits, em.min_q);
+        d, keys, flags, evout, queue, em.bits, em.min_q, nullptr);
     if (t) t->end(KK_INSERT_EVICT, s);
     return cudaGetLastError();
   }

@@ -32,7 +32,12 @@ struct Ctrl {
   unsigned long long cas_retry[7];
   // Bounds-checked builds: the first out-of-range bucket index + 1 (0: none).
   unsigned long long debug_bad_index;
-  unsigned long long pad[10];
+  // Slice-grouped eviction levels that ran, the chain steps they took, and
+  // the chains run to their end for want of room in a level's buffer.
+  unsigned long long level_passes;
+  unsigned long long level_steps;
+  unsigned long long level_runout;
+  unsigned long long pad[7];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is 256 bytes");
 
@@ -59,6 +64,24 @@ struct DevFilter {
 
 constexpr uint32_t kSliceMax = 1024;  // slices per table (shared-memory bins)
 constexpr uint32_t kFill2Extra = 3;   // counters after the S per-slice ones
+
+// Scratch of the slice-grouped eviction levels (see cf_levels.cuh): two
+// record buffers used in turn, each S slice regions of cap records and a
+// spill region of spill records, 3 words per record; per level (L + 1 sets)
+// S + 2 counters one per 128-byte line (the S slice fills, the spill fill,
+// the tile counter); ctl[0] = 1 when this launch runs the levels, ctl[1 + k]
+// = records at the start of level k (k = 0..L).
+struct LevelBufs {
+  uint64_t* rec[2];
+  uint32_t* fill;
+  uint32_t* ctl;
+  uint64_t cap;
+  uint64_t spill;
+  uint32_t n_levels;  // L
+  uint32_t min_q;     // the levels run when at least this many keys are queued
+  uint32_t stop_q;    // level k >= 1 runs only with at least this many records
+  uint32_t pad;
+};
 
 // Device scratch of the slice-partitioned path for chunks of up to n keys
 // (see cf_slice.cuh).

@@ -217,6 +217,15 @@ class CuckooFilter:
         check(self._L.cf_set_eviction_map(self._h, modes[mode], int(min_queue)),
               "cf_set_eviction_map")
 
+    def set_eviction_levels(self, mode: str = "on", n_levels: int = 0, min_queue: int = 0,
+                            stop_queue: int = 0):
+        """Slice-grouped eviction levels of the sliced insert: "off" or "on"
+        (cf_set_eviction_levels); 0 takes the library defaults."""
+        code = {"off": 0, "on": 1}[mode]
+        check(self._L.cf_set_eviction_levels(self._h, code, int(n_levels), int(min_queue),
+                                             int(stop_queue)),
+              "cf_set_eviction_levels")
+
     def set_cas_limit(self, limit: int = 0):
         """Test knob: bound of the CAS retry loops (0 = default 4096)."""
         check(self._L.cf_debug_set_cas_limit(self._h, int(limit)), "cf_debug_set_cas_limit")

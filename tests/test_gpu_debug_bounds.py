@@ -5,9 +5,10 @@ clamped, never trapped).
 * In the normal build the touch export refuses an index beyond the table on
   the host.
 * The checked build is built, and the small parity suites (plain and sliced
-  paths, the full-bucket map, batched launches) run against it in a
-  subprocess, with every filter audited for bounds violations after each
-  test; the checked build's own check is shown to catch a planted bad index.
+  paths, the full-bucket map, the eviction levels, batched launches) run
+  against it in a subprocess, with every filter audited for bounds
+  violations after each test; the checked build's own check is shown to
+  catch a planted bad index.
 """
 import os
 import subprocess
@@ -73,6 +74,7 @@ def test_parity_suites_under_the_checked_build():
            os.path.join(ROOT, "tests", "test_gpu_parity.py"),
            os.path.join(ROOT, "tests", "test_gpu_slice.py"),
            os.path.join(ROOT, "tests", "test_gpu_evict_map.py"),
+           os.path.join(ROOT, "tests", "test_gpu_levels.py"),
            os.path.join(ROOT, "tests", "test_gpu_batched.py"),
            os.path.join(ROOT, "tests", "test_gpu_debug_bounds.py"),
            "-k", "not cas_limit and not parity_suites_under"]

@@ -3,8 +3,8 @@ the small parity tests do not reach at size:
 
 * a 2^25-bucket table (f16 b4, 256 MiB) filled to LF 0.95 in three calls
   through the library's automatic choices: the slice-partitioned path with
-  its default 32 MiB slices and default pass size, and the full-bucket map
-  of the eviction loop;
+  its default 32 MiB slices and default pass size, the full-bucket map and
+  the slice-grouped eviction levels;
 * a 2^24-bucket table (128 MiB) with slicing off, filled in batches below
   m/8 keys: the plain direct-insert, eviction and delete kernels in their
   DRAM-resident build (the one the serving loop runs on large filters),
@@ -75,6 +75,8 @@ def test_auto_path_at_2_25_buckets_multiset():
     o = oracle.OracleFilter(m, f, b, 500)
     st = _check_multiset(g, o, keys, m, f, b, flags.cpu().numpy())
     assert st["evictions"] > 0
+    # The last fills' queues (millions of keys) take the eviction levels.
+    assert kt["evict_level"][0] >= 1 and st["level_passes"] > 0
 
 
 def test_plain_dram_kernels_at_2_24_buckets_multiset_and_delete():
