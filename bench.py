@@ -46,7 +46,7 @@ DEFAULT_LEVELS = 12
 # null until the capture is taken again).
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_large_2^28x4_f16_lf0.95.md")
 KERNEL_SOURCES = ("cf_types.h", "cf_device.cuh", "cf_kernels.cuh", "cf_slice.cuh",
-                  "cf_inst_f16.cu")
+                  "cf_levels.cuh", "cf_launch.cuh", "cf_inst_f16.cu")
 
 
 def kernel_sources_sha() -> str:
@@ -1241,8 +1241,9 @@ def main(argv=None):
                     help="slice-partitioned execution of the filter calls (cf_set_slicing)")
     ap.add_argument("--evict-map", choices=["off", "auto", "always"], default="auto",
                     help="full-bucket map of the eviction loop (cf_set_eviction_map)")
-    ap.add_argument("--evict-levels", choices=["off", "on"], default="on",
-                    help="slice-grouped eviction levels (cf_set_eviction_levels)")
+    ap.add_argument("--evict-levels", choices=["off", "on", "always"], default="on",
+                    help="slice-grouped eviction levels (cf_set_eviction_levels; \"on\": "
+                         "device-buffer inserts, \"always\": the host-buffer ones too)")
     ap.add_argument("--levels", type=int, default=0,
                     help="eviction levels per insert pass (0: the library default, 12)")
     ap.add_argument("--slice-bytes", type=int, default=0,

@@ -134,7 +134,7 @@ struct cf_filter {
   uint32_t* fullmap = nullptr;
   // Slice-grouped eviction levels (cf_set_eviction_levels): mode, levels,
   // thresholds (0: defaults) and the record buffers (allocated on first use).
-  int lv_mode = 1;                     // 0 off, 1 on (sliced BFS inserts with the map)
+  int lv_mode = 1;                     // 0 off, 1 device-buffer calls, 2 all calls
   uint32_t lv_levels = 0;
   uint64_t lv_min_queue = 0;
   uint64_t lv_stop_queue = 0;

@@ -219,9 +219,11 @@ class CuckooFilter:
 
     def set_eviction_levels(self, mode: str = "on", n_levels: int = 0, min_queue: int = 0,
                             stop_queue: int = 0):
-        """Slice-grouped eviction levels of the sliced insert: "off" or "on"
-        (cf_set_eviction_levels); 0 takes the library defaults."""
-        code = {"off": 0, "on": 1}[mode]
+        """Slice-grouped eviction levels of the sliced insert
+        (cf_set_eviction_levels): "off", "on" (device-buffer inserts; the
+        default) or "always" (host-buffer inserts too); 0 takes the library
+        defaults."""
+        code = {"off": 0, "on": 1, "always": 2}[mode]
         check(self._L.cf_set_eviction_levels(self._h, code, int(n_levels), int(min_queue),
                                              int(stop_queue)),
               "cf_set_eviction_levels")

@@ -16,7 +16,8 @@ asked of the full-bucket map).  So:
   * a batch skewed into one slice overflows a level's buffer: those chains
     run to their end at once, and the invariants still hold;
   * the levels run only when switched on, for BFS, with the map, and for
-    queues of at least min_queue keys.
+    queues of at least min_queue keys; host-buffer inserts take them only
+    in the "always" mode.
 """
 import numpy as np
 import pytest
@@ -188,3 +189,19 @@ def test_levels_rules(cf):
         g.set_eviction_levels("bogus")
     with pytest.raises(Exception):
         g.set_eviction_levels("on", 257)
+
+
+@pytest.mark.parametrize("mode,runs", [("on", False), ("always", True)])
+def test_levels_on_host_buffer_calls(cf, mode, runs):
+    """Host-buffer inserts keep the eviction loop in the default mode (the
+    levels slow the copies beside them) and take the levels in "always";
+    the results are valid either way."""
+    m, f, b = 1 << 12, 16, 4
+    ks = workloads.keys(909, int(0.96 * m * b))
+    o = oracle.OracleFilter(m, f, b, 500)
+    g = _levels_filter(cf, m, f, b)
+    g.set_eviction_levels(mode, 0, 1, 1)
+    g.set_staging_chunk(4096)
+    flags = g.insert_host(ks)
+    st = _check(cf, g, o, ks, flags, "xor", m, f, b)
+    assert (st["level_passes"] > 0) == runs and st["evictions"] > 0
