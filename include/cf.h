@@ -285,7 +285,7 @@ cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue);
  * chains (0: 2^18), the remaining chains run to their end as in the loop.
  * The library allocates two record buffers of about 12 bytes per key of a
  * pass each on first use (freed by cf_destroy, or here when n_levels
- * changes).  mode: 0 off; 1 (the default) for inserts of device buffers
+ * changes); if that allocation fails, the insert runs the loop instead.  mode: 0 off; 1 (the default) for inserts of device buffers
  * only: beside the host-buffer calls' copies the levels slow those copies
  * more than they save (measured: 15-45% more copy time per step of the
  * large workload), so those calls keep the loop; 2 for every sliced insert.

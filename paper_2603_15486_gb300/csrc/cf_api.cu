@@ -420,8 +420,8 @@ cf_status evict_map_for(cf_filter* f, cfk::EvictMap* em, uint64_t level_n = 0) {
   em->bits = f->fullmap;
   em->min_q = map_min_queue(f);
   if (level_n) {
-    st = ensure_levels(f, level_n);
-    if (st != CF_OK) return st;
+    // Without room for the level buffers the insert keeps the loop.
+    if (ensure_levels(f, level_n) != CF_OK) return CF_OK;
     em->lv = f->lv;
     em->lv.min_q = clamp_u32(f->lv_min_queue ? f->lv_min_queue : kLevelMinQueue);
     em->lv.stop_q = clamp_u32(f->lv_stop_queue ? f->lv_stop_queue : kLevelStopQueue);

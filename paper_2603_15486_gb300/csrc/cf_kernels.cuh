@@ -793,8 +793,9 @@ int device_sm_count();
 int cached_occupancy(const void* fn, int block);
 
 template <class F>
-inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block) {
-  const int occ = cached_occupancy(reinterpret_cast<const void*>(fn), kBlock);
+inline unsigned persistent_grid(F* fn, uint64_t work_items, int per_block,
+                                int block = kBlock) {
+  const int occ = cached_occupancy(reinterpret_cast<const void*>(fn), block);
   const uint64_t cap = uint64_t(device_sm_count()) * uint64_t(occ > 0 ? occ : 1);
   uint64_t need = (work_items + per_block - 1) / per_block;
   if (need < 1) need = 1;

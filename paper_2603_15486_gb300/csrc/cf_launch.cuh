@@ -29,21 +29,22 @@ struct SliceLaunch {
   static cudaError_t probes(const DevFilter& d, const SliceBufs& sb, uint64_t n,
                             int want, uint32_t* queue, cudaStream_t s,
                             KernelTimer* t) {
-    constexpr uint32_t T = kBlock * 8;
+    constexpr uint32_t T = kSliceBlock * 8;
     const size_t smem = size_t(20) * T + size_t(24) * sb.n_slices + 16;
     const bool rt = d.max_cas != kMaxCas;
     auto p1 = rt ? k_slice_probe1<G, OP, K, true> : k_slice_probe1<G, OP, K>;
     cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(p1), smem);
     if (e != cudaSuccess) return e;
     if (t) t->begin(KK_SLICE_PROBE1, s);
-    p1<<<persistent_grid(p1, n, T), kBlock, smem, s>>>(d, sb, want);
+    p1<<<persistent_grid(p1, n, T, kSliceBlock), kSliceBlock, smem, s>>>(d, sb, want);
     if (t) t->end(KK_SLICE_PROBE1, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto p2 = rt ? k_slice_probe2<G, OP, K, true> : k_slice_probe2<G, OP, K>;
     const size_t smem2 = size_t(2) * (sb.n_slices + 1) * sizeof(uint32_t);
     if (t) t->begin(KK_SLICE_PROBE2, s);
-    p2<<<persistent_grid(p2, n, kBlock * 8), kBlock, smem2, s>>>(d, sb, n, want, queue);
+    p2<<<persistent_grid(p2, n, kSliceBlock * 8, kSliceBlock), kSliceBlock, smem2, s>>>(
+        d, sb, n, want, queue);
     if (t) t->end(KK_SLICE_PROBE2, s);
     return cudaGetLastError();
   }

@@ -78,6 +78,11 @@ enum : int { SOP_INSERT = 0, SOP_CONTAINS = 1, SOP_REMOVE = 2 };
 #ifndef CF_SLICE2_MINB
 #define CF_SLICE2_MINB CF_SLICE_MINB
 #endif
+// Threads per block of the bucket passes (probe1 / probe2).
+#ifndef CF_SLICE_BLOCK
+#define CF_SLICE_BLOCK 256
+#endif
+constexpr int kSliceBlock = CF_SLICE_BLOCK;
 // Minimum resident blocks per SM of the scatter: 4 (64 registers) ran the
 // split in 17.4 ms per step against 18.1 at the compiler's own choice.
 #ifndef CF_SPLIT_MINB
@@ -301,25 +306,25 @@ k_slice_scatter(DevFilter d, const uint64_t* __restrict__ keys, uint64_t n,
 
 // ---------------------------------------------------------------------------
 // probe1: the operation on bucket i1 for rec1 records, regions in order.  A
-// block tile is up to kBlock*8 records of one region (thread t takes
-// records t, t + kBlock, ...), staged in shared memory by a TMA bulk copy
+// block tile is up to kSliceBlock*8 records of one region (thread t takes
+// records t, t + kSliceBlock, ...), staged in shared memory by a TMA bulk copy
 // issued while the block works on the previous tile.  Records left pending
 // are stashed in shared memory, sorted by the slice of i2 once per tile,
 // and written to rec2 as one run per occupied slice (one claim on fill2 per
 // run).
 // Shared memory: 20*T bytes + 4*S counters + 4*(S + 2) tile starts +
-// 4*(S + 1) region lengths (T = kBlock*8 = 2048 records).
+// 4*(S + 1) region lengths (T = kSliceBlock*8 records).
 // ---------------------------------------------------------------------------
 
 template <class G, int OP, int K, bool RT = false>
-__global__ void __launch_bounds__(kBlock, CF_SLICE_MINB)
+__global__ void __launch_bounds__(kSliceBlock, CF_SLICE_MINB)
 k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
   // R rounds of K records per thread: every tile holds 8 records per thread
   // whatever the bucket size (K = 8 / 4 / 2 / 1 for 8 / 16 / 32 / 64-byte
   // buckets), so the per-tile work (barriers, prefix, claims) stays amortised.
   constexpr int R = 8 / K;
   constexpr int N = R * K;
-  constexpr uint32_t T = kBlock * N;
+  constexpr uint32_t T = kSliceBlock * N;
   static_assert(K == 8 || K == 4 || K == 2 || K == 1, "records per thread");
   static_assert(T <= 2048, "shared entries pack an 11-bit tile index");
   extern __shared__ uint64_t sm64[];
@@ -382,7 +387,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
   while (tcnt) {
     const bool copy_ok = mbar_wait(&s_bar, parity);
     parity ^= 1u;
-    // Record i of this thread: tile index loc(i) = i*kBlock + thread (lane-
+    // Record i of this thread: tile index loc(i) = i*kSliceBlock + thread (lane-
     // strided: conflict-free reads of the staged tile, coalesced stores),
     // at rec1 position t0 + loc.
     const uint32_t copied = tcnt & ~1u;  // records now in pref
@@ -390,7 +395,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
     bool vr[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
+      const uint32_t loc = uint32_t(i) * kSliceBlock + threadIdx.x;
       vr[i] = loc < tcnt;
       hr[i] = loc < copied ? pref[loc] : (vr[i] ? ld_stream_u64(sb.rec1 + t0 + loc) : 0ull);
     }
@@ -433,7 +438,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int i = r * K + k;
-        const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
+        const uint32_t loc = uint32_t(i) * kSliceBlock + threadIdx.x;
         slrk[i] = kSettled;  // settled with flag 0 (or not a record)
         if (valid[k] && res[k] == TI_FULL) {
           const uint32_t sl = alt_index<G>(d, bkt[k], tag[k]) >> sb.shift;
@@ -465,7 +470,7 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
     };
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const uint32_t loc = uint32_t(i) * kBlock + threadIdx.x;
+      const uint32_t loc = uint32_t(i) * kSliceBlock + threadIdx.x;
       uint32_t lk = slrk[i];
       if (lk < kSettled) {
         const uint32_t sl = lk >> 16, rk = lk & 0xFFFFu;
@@ -503,11 +508,11 @@ k_slice_probe1(DevFilter d, SliceBufs sb, int want_flags) {
 // probe2: the operation on bucket i2 for the rec2 records, slice regions in
 // order, then the spill region.  The filled parts of the regions are
 // numbered consecutively (a prefix of their fills in shared memory), and
-// block tiles of kBlock*8 of those numbers are handed out in order by a
+// block tiles of kSliceBlock*8 of those numbers are handed out in order by a
 // counter, so that only records are visited.
 // ---------------------------------------------------------------------------
 template <class G, int OP, int K, bool RT = false>
-__global__ void __launch_bounds__(kBlock, CF_SLICE2_MINB)
+__global__ void __launch_bounds__(kSliceBlock, CF_SLICE2_MINB)
 k_slice_probe2(DevFilter d, SliceBufs sb, uint64_t n, int want_flags,
                uint32_t* __restrict__ queue) {
   // The filled part of each region (S slices, then the spill region) and
