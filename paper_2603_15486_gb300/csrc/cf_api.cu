@@ -420,8 +420,12 @@ cf_status evict_map_for(cf_filter* f, cfk::EvictMap* em, uint64_t level_n = 0) {
   em->bits = f->fullmap;
   em->min_q = map_min_queue(f);
   if (level_n) {
-    // Without room for the level buffers the insert keeps the loop.
-    if (ensure_levels(f, level_n) != CF_OK) return CF_OK;
+    // Without room for the level buffers the insert keeps the loop (and
+    // the failed allocation is not the call's error).
+    if (ensure_levels(f, level_n) != CF_OK) {
+      g_err[0] = 0;
+      return CF_OK;
+    }
     em->lv = f->lv;
     em->lv.min_q = clamp_u32(f->lv_min_queue ? f->lv_min_queue : kLevelMinQueue);
     em->lv.stop_q = clamp_u32(f->lv_stop_queue ? f->lv_stop_queue : kLevelStopQueue);
@@ -815,7 +819,7 @@ cf_status cf_debug_set_cas_limit(cf_filter* f, uint32_t limit) {
   return CF_OK;
 }
 
-int cf_version(void) { return 10100; }
+int cf_version(void) { return 10200; }
 
 const char* cf_status_str(cf_status s) {
   switch (s) {
