@@ -237,6 +237,23 @@ def kernel_bytes(phases: dict, bucket_bytes: int, n_insert: int, n_query: int,
             "remove": n_delete * ((d["bucket_reads"] + d["bucket_writes"]) / d["ops"] * spb + 9)}
 
 
+def merge_eviction_times(ktimes: dict, kb: dict, steps: int):
+    """The eviction (Alg. 1 phase 2) of a sliced insert runs as the slice-
+    grouped levels and the loop for what they leave: one entry "eviction"
+    (the levels' timer records as its launches, the two kinds' time, the
+    eviction's algorithmic bytes) and its split per step.  Without level
+    records the times stay as they are (None for the split)."""
+    ktimes = dict(ktimes)
+    lv = ktimes.pop("evict_level", (0, 0.0))
+    if not lv[0]:
+        return ktimes, None
+    _, ms_loop = ktimes.pop("insert_evict", (0, 0.0))
+    ktimes["eviction"] = (lv[0], ms_loop + lv[1])
+    kb["eviction"] = kb["insert_evict"]
+    return ktimes, {"levels_ms_per_step": round(lv[1] / steps, 3),
+                    "loop_and_rest_ms_per_step": round(ms_loop / steps, 3)}
+
+
 def slice_kernel_bytes(phases: dict, W, chunk: int) -> dict:
     """Bytes the slice-partitioned passes must move per step (their streams,
     plus one sweep of the table per bucket pass: read, and written back for
@@ -445,18 +462,7 @@ def gpu_arm(args):
     # (the counters restart with every step's clear, so st_end holds one
     # step's builds).
     kb["evict_map"] = st_end["map_builds"] * (W.table_bytes + (W.m + 31) // 32 * 4)
-    # The eviction (Alg. 1 phase 2) of a sliced insert runs as the slice-
-    # grouped levels and the loop for the queues they leave: one entry
-    # ("eviction", the loop's launches) with the eviction's algorithmic bytes.
-    ktimes = dict(ktimes)
-    lv = ktimes.pop("evict_level", (0, 0.0))
-    evict_parts = None
-    if lv[0]:
-        le, mse = ktimes.pop("insert_evict", (0, 0.0))
-        ktimes["eviction"] = (lv[0], mse + lv[1])
-        kb["eviction"] = kb["insert_evict"]
-        evict_parts = {"levels_ms_per_step": round(lv[1] / args.steps, 3),
-                       "loop_and_rest_ms_per_step": round(mse / args.steps, 3)}
+    ktimes, evict_parts = merge_eviction_times(ktimes, kb, args.steps)
     peak = peaks.get("hbm_gbs") or 6800.0
     kern = {}
     for k, (launches, ms) in ktimes.items():

@@ -67,6 +67,21 @@ def test_bytes_per_op_model():
     assert b64["query"] == 1.5 * 64 + 9
 
 
+def test_eviction_times_merge_levels_and_loop():
+    sys.path.insert(0, ROOT)
+    import bench
+    kb = {"insert_evict": 50e9, "slice_probe1": 1.0}
+    kt = {"insert_evict": (10, 30.0), "evict_level": (5, 70.0), "slice_probe1": (10, 5.0)}
+    got, parts = bench.merge_eviction_times(kt, kb, 5)
+    assert got == {"slice_probe1": (10, 5.0), "eviction": (5, 100.0)}
+    assert kb["eviction"] == 50e9
+    assert parts == {"levels_ms_per_step": 14.0, "loop_and_rest_ms_per_step": 6.0}
+    # Without level records (levels off, or the plain path) nothing changes.
+    kt2 = {"insert_evict": (10, 30.0), "evict_level": (0, 0.0)}
+    got2, parts2 = bench.merge_eviction_times(kt2, {"insert_evict": 1.0}, 5)
+    assert got2 == {"insert_evict": (10, 30.0)} and parts2 is None
+
+
 def test_slice_stream_byte_model():
     """Per-pass stream bytes of the sliced path, worked by hand for a table
     of 1000 bytes and one call per operation: 100 inserts (half pending
