@@ -568,6 +568,7 @@ def e2e_run(filt, keys, queries, W, args, stream):
     hq.copy_(queries)
     segs = W.insert_segments()
     filt.set_staging_chunk(args.e2e_chunk)
+    filt.set_host_reads(args.e2e_reads)
     # The host-to-device link's copy rate, measured outside the timed
     # region (four back-to-back copies of up to 1 GiB of the pinned keys),
     # for reading E beside it.
@@ -612,6 +613,7 @@ def e2e_run(filt, keys, queries, W, args, stream):
             "steps": args.e2e_steps, "pinned": pinned,
             "ms_per_step": round(el / args.e2e_steps * 1e3, 3),
             "staging_chunk": args.e2e_chunk,
+            "host_reads": args.e2e_reads,
             "h2d_link_GBps": round(link_gbps, 1),
             "api": "cf_insert_host_async / cf_contains_host_async / cf_remove_host_async "
                    "(pinned host keys in, host flags out; one stream synchronisation after "
@@ -1237,6 +1239,9 @@ def main(argv=None):
     ap.add_argument("--extras-requests", type=int, default=1000,
                     help="requests of the served-vs-plain summary trace")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-reads", choices=["staged", "in_place"], default="staged",
+                    help="how the end-to-end leg's sliced passes get their keys "
+                         "(cf_set_host_reads)")
     ap.add_argument("--e2e-warmup", type=int, default=1)
     ap.add_argument("--e2e-chunk", type=int, default=1 << 27,
                     help="keys per staging chunk of the host-buffer calls (eight "

@@ -109,6 +109,7 @@ SIGNATURES = {
     "cf_set_slicing": (_st, [_vp, _int, _u64, _u64]),
     "cf_set_eviction_map": (_st, [_vp, _int, _u64]),
     "cf_set_eviction_levels": (_st, [_vp, _int, ctypes.c_uint32, _u64, _u64]),
+    "cf_set_host_reads": (_st, [_vp, _int]),
     "cf_debug_set_cas_limit": (_st, [_vp, _u32]),
     "cf_debug_bounds_checked": (_int, []),
     "cf_debug_touch_bucket": (_st, [_vp, _u64, ctypes.POINTER(_u64), _vp]),

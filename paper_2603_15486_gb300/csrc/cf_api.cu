@@ -614,6 +614,20 @@ cf_status flush_group(cf_filter* f, cfk::FlagGroup* g, uint8_t* dst_h, uint64_t 
   return CF_OK;
 }
 
+// The device address at which kernels can read host keys in place: pinned
+// host memory mapped into the device's address space; null for any other
+// buffer (which takes the staged copies).
+const uint64_t* host_keys_in_place(const uint64_t* keys_h) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, keys_h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer)
+    return static_cast<const uint64_t*>(a.devicePointer);
+  return nullptr;
+}
+
 // Sliced path: passes of up to the filter's pass size; each pass's keys
 // arrive in staging chunks, each scattered as it lands, then the pass's
 // bucket passes, eviction loop and result passes run once, and the pass's
@@ -640,10 +654,15 @@ cf_status host_sliced(cf_filter* f, Op op, const uint64_t* keys_h, uint64_t n,
     if (st != CF_OK) return st;
   }
   const uint64_t chunk = f->stage_chunk;
+  // In-place reads (cf_set_host_reads): the scatter reads the pass's keys
+  // over the host link itself, with no copy engine and no staging.
+  const uint64_t* kd = f->host_reads ? host_keys_in_place(keys_h) : nullptr;
   for (uint64_t p0 = 0; p0 < n; p0 += plen) {
     const uint64_t pl = (n - p0) < plen ? (n - p0) : plen;
     cudaError_t e = f->ops->sliced_begin(f->sb, s);
-    for (uint64_t c0 = 0; c0 < pl && e == cudaSuccess; c0 += chunk) {
+    if (kd && e == cudaSuccess)
+      e = f->ops->sliced_scatter(f->d, kd + p0, pl, 0, flags_h != nullptr, f->sb, s, f->timer);
+    for (uint64_t c0 = 0; !kd && c0 < pl && e == cudaSuccess; c0 += chunk) {
       const uint64_t len = (pl - c0) < chunk ? (pl - c0) : chunk;
       Stage* sg = nullptr;
       st = stage_keys(f, keys_h + p0 + c0, len, s, &sg);
@@ -797,6 +816,12 @@ cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue) {
   if (!f || mode < 0 || mode > 2) return CF_EINVAL;
   f->map_mode = mode;
   f->map_min_queue = min_queue;
+  return CF_OK;
+}
+
+cf_status cf_set_host_reads(cf_filter* f, int mode) {
+  if (!f || mode < 0 || mode > 1) return CF_EINVAL;
+  f->host_reads = mode;
   return CF_OK;
 }
 

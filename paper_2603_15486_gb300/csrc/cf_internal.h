@@ -118,6 +118,7 @@ struct cf_filter {
   uint32_t next_slot = 0;     // staging slot and flag group used next
   uint32_t next_group = 0;
   cudaStream_t s_in = nullptr, s_out = nullptr;
+  int host_reads = 0;  // cf_set_host_reads: 0 staged copies, 1 sliced passes read pinned keys in place
   bool stage_ready = false;
   cfk::FilterTimer* timer = nullptr;  // non-null while kernel timing is on
   // Slice-partitioned path (cf_set_slicing): mode, geometry, scratch.

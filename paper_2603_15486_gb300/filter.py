@@ -202,6 +202,12 @@ class CuckooFilter:
     def set_staging_chunk(self, keys_per_chunk: int):
         check(self._L.cf_set_staging_chunk(self._h, int(keys_per_chunk)), "cf_set_staging_chunk")
 
+    def set_host_reads(self, mode: str = "staged"):
+        """How sliced host-buffer calls get their keys (cf_set_host_reads):
+        "staged" copies or "in_place" reads of pinned keys by the scatter."""
+        check(self._L.cf_set_host_reads(self._h, {"staged": 0, "in_place": 1}[mode]),
+              "cf_set_host_reads")
+
     def set_slicing(self, mode: str = "auto", slice_bytes: int = 0, max_chunk: int = 0):
         """Slice-partitioned execution (cf_set_slicing): mode "off", "auto"
         or "always"; slice_bytes / max_chunk 0 take the library defaults."""

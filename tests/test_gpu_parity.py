@@ -413,19 +413,24 @@ def test_host_buffer_api_matches_device_api(cf):
     assert g.stats()["remove_ok"] == 5000
 
 
+@pytest.mark.parametrize("reads", ["staged", "in_place"])
 @pytest.mark.parametrize("slicing", ["off", "always"])
-def test_async_host_calls_match_device_calls(cf, slicing):
+def test_async_host_calls_match_device_calls(cf, slicing, reads):
     """The asynchronous host-buffer calls, issued back to back without a
     synchronisation in between (insert, query, delete, query), give what
     the device calls give on the same table.  With slicing forced, passes of
     5000 keys gather their keys in staging chunks of 1777, so every pass is
-    split across several chunks and the chunks across passes."""
+    split across several chunks and the chunks across passes; or, with
+    in-place reads, the scatter reads the pinned keys over the host link
+    (no key copies at all)."""
     m, f, b = 1 << 12, 16, 4
     ks = workloads.keys(57, int(0.9 * m * b))
     neg = workloads.keys(57, 9000, start=ks.size)
     q = np.concatenate([ks, neg])
     g = cf.CuckooFilter(m, f, b, 500)
     g.set_staging_chunk(1777)
+    g.set_host_reads(reads)
+    g.set_kernel_timing(True)
     if slicing == "always":
         g.set_slicing("always", 1024, 5000)
     hk = torch.from_numpy(ks.view(np.int64)).pin_memory()
@@ -440,6 +445,8 @@ def test_async_host_calls_match_device_calls(cf, slicing):
     g.remove_host_async(hk[:4000], out=fd, stream=st)
     g.contains_host_async(hq, out=fq2, stream=st)
     st.synchronize()
+    h2d = g.kernel_times()["copy_h2d"][0]
+    assert (h2d == 0) == (reads == "in_place" and slicing == "always")
     flags = fi.numpy()
     # The inserts: the invariants on the table as it stood after them are
     # checked through the first query (every key found) and the counters.
@@ -457,6 +464,22 @@ def test_async_host_calls_match_device_calls(cf, slicing):
     ot = oracle.OracleFilter(m, f, b, 500)
     ot.load(g.snapshot())
     assert np.array_equal(ot.contains_batch(q), fq2.numpy())
+
+
+def test_in_place_reads_fall_back_to_copies_for_pageable_keys(cf):
+    """In-place reads take only pinned keys; a pageable numpy buffer keeps
+    the staged copies, with the same results."""
+    m, f, b = 1 << 12, 16, 4
+    ks = workloads.keys(59, int(0.9 * m * b))
+    g = cf.CuckooFilter(m, f, b, 500)
+    g.set_slicing("always", 1024, 5000)
+    g.set_host_reads("in_place")
+    g.set_kernel_timing(True)
+    fl = g.insert_host(ks)
+    assert (fl == 1).all() and g.kernel_times()["copy_h2d"][0] > 0
+    assert g.contains_host(ks).all()
+    with pytest.raises(Exception):
+        g.set_host_reads("bogus")
 
 
 def test_create_at_caller_memory(cf):
