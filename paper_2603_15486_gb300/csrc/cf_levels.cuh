@@ -113,10 +113,6 @@ __device__ __forceinline__ bool lv_runs(const LevelBufs& lb, uint32_t k) {
   return k == 0 || __ldcg(lb.ctl + 1 + k) >= lb.stop_q;
 }
 
-// One step of a chain at bucket c.cur (words c.bk), see the file comment.
-// mark: c.cur's map bit may be clear.  Returns EV_OK, EV_FAIL or
-// EV_CONTENTION (vt/vb the victim), or ROUND_CONTINUE with c at the
-// evicted tag's bucket and mark_out for that bucket.
 // The place part of a step: EV_OK or EV_CONTENTION (vt/vb the victim) if
 // the chain ended, else ROUND_CONTINUE with c.cur full (and its map bit set
 // when mark).
@@ -141,6 +137,10 @@ __device__ __forceinline__ int lv_place(const DevFilter& d, uint32_t* map, Chain
   return ROUND_CONTINUE;
 }
 
+// One step of a chain at bucket c.cur (words c.bk), see the file comment.
+// mark: c.cur's map bit may be clear.  Returns EV_OK, EV_FAIL or
+// EV_CONTENTION (vt/vb the victim), or ROUND_CONTINUE with c at the
+// evicted tag's bucket and mark_out for that bucket.
 template <class G>
 __device__ __forceinline__ int lv_step(const DevFilter& d, uint32_t* map, Chain<G>& c,
                                        bool mark, uint32_t& vt, uint64_t& vb,
@@ -193,7 +193,6 @@ __device__ void lv_run_out(const DevFilter& d, uint32_t* map, uint8_t* f2, const
   }
   lv_end(d, f2, rec.idx, r, c.ev, vt, vb, n);
 }
-template <class G>
 __device__ __forceinline__ void lv_counts_flush(const DevFilter& d, const LvCounts& n) {
   block_add(&d.ctrl->occupancy, n.ok);
   block_add(&d.ctrl->insert_ok, n.ok);
@@ -329,7 +328,7 @@ k_evict_seed(DevFilter d, const uint64_t* __restrict__ rec2, const uint32_t* __r
     __syncthreads();
     lv_split_out<G, N>(d, map, f2, sp, slrk, S, fill, lb, lb.rec[0], lb.ctl + 1, n, tmp);
   }
-  lv_counts_flush<G>(d, n);
+  lv_counts_flush(d, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -445,7 +444,7 @@ k_evict_level(DevFilter d, uint32_t* map, LevelBufs lb, uint32_t S, uint32_t shi
     __syncthreads();
     lv_split_out<G, N>(d, map, f2, sp, slrk, S, fout, lb, out, lb.ctl + 2 + k, n, tmp);
   }
-  lv_counts_flush<G>(d, n);
+  lv_counts_flush(d, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -541,7 +540,7 @@ k_evict_resume(DevFilter d, uint32_t* map, LevelBufs lb, uint32_t S, uint8_t* f2
       }
     }
   }
-  lv_counts_flush<G>(d, n);
+  lv_counts_flush(d, n);
 }
 
 }  // namespace cfk
