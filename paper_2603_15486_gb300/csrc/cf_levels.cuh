@@ -51,14 +51,26 @@
 
 namespace cfk {
 
-// Minimum resident blocks per SM of the level kernels, and records per
-// thread of a level tile for buckets of up to 8 bytes (halved for 16-byte
-// buckets, one for larger ones).
-#ifndef CF_LEVEL_MINB
-#define CF_LEVEL_MINB 3
-#endif
+// Records per thread of a level tile and resident blocks per SM of the
+// level kernels, for buckets of up to 8 bytes (CF_LEVEL_N, CF_LEVEL_MINB)
+// and for wider ones (one record per thread, CF_LEVEL_MINB_WIDE).  Large
+// workload, eviction ms per step (records per thread x blocks per SM):
+// 4 x 3: 35.5, 8 x 2: 41.4, 2 x 4: 32.6, 2 x 5: 30.9, 2 x 6: 31.1, 2 x 8
+// (spilling): 34.6, 1 x 6: 32.6.  The steps are bound by random sector
+// reads: more warps with fewer records each keep more of them in flight.
+// Wider buckets spill above 3 blocks per SM.
 #ifndef CF_LEVEL_N
-#define CF_LEVEL_N 4
+#define CF_LEVEL_N 2
+#endif
+#ifndef CF_LEVEL_MINB
+#define CF_LEVEL_MINB 5
+#endif
+#ifndef CF_LEVEL_MINB_WIDE
+#define CF_LEVEL_MINB_WIDE 3
+#endif
+// Resident blocks per SM of the seed (four records per thread).
+#ifndef CF_SEED_MINB
+#define CF_SEED_MINB 3
 #endif
 
 // A chain record: 3 words (rng; cur | tag << 32; idx | (ev | mark << 31) << 32).
@@ -293,7 +305,7 @@ __device__ void lv_split_out(const DevFilter& d, uint32_t* map, uint8_t* f2, con
 // than the buffer's slice regions hold.
 // ---------------------------------------------------------------------------
 template <class G>
-__global__ void __launch_bounds__(kBlock, CF_LEVEL_MINB)
+__global__ void __launch_bounds__(kBlock, CF_SEED_MINB)
 k_evict_seed(DevFilter d, const uint64_t* __restrict__ rec2, const uint32_t* __restrict__ queue,
              uint32_t* map, uint32_t map_q, LevelBufs lb, uint32_t S, uint32_t shift,
              uint8_t* f2) {
@@ -340,14 +352,13 @@ k_evict_seed(DevFilter d, const uint64_t* __restrict__ rec2, const uint32_t* __r
 // ---------------------------------------------------------------------------
 template <class G>
 struct LvTile {
-  static constexpr int N = G::kBucketBytes <= 8    ? CF_LEVEL_N
-                           : G::kBucketBytes <= 16 ? (CF_LEVEL_N + 1) / 2
-                                                   : 1;
+  static constexpr int N = G::kBucketBytes <= 8 ? CF_LEVEL_N : 1;
+  static constexpr int kMinB = G::kBucketBytes <= 8 ? CF_LEVEL_MINB : CF_LEVEL_MINB_WIDE;
   static constexpr uint32_t T = kBlock * N;
 };
 
 template <class G>
-__global__ void __launch_bounds__(kBlock, CF_LEVEL_MINB)
+__global__ void __launch_bounds__(kBlock, LvTile<G>::kMinB)
 k_evict_level(DevFilter d, uint32_t* map, LevelBufs lb, uint32_t S, uint32_t shift,
               uint32_t k, uint8_t* f2) {
   constexpr int N = LvTile<G>::N;
