@@ -325,7 +325,7 @@ def gpu_arm(args):
     filt = CuckooFilter(W.m, W.f, W.b, W.max_evictions)
     filt.set_slicing(args.slicing, args.slice_bytes, args.slice_chunk)
     filt.set_eviction_map(args.evict_map)
-    filt.set_eviction_levels(args.evict_levels, args.levels)
+    filt.set_eviction_levels(args.evict_levels, args.levels, 0, args.level_stop)
     stream.synchronize()
 
     segs = W.insert_segments()
@@ -1263,6 +1263,8 @@ def main(argv=None):
                          "device-buffer inserts, \"always\": the host-buffer ones too)")
     ap.add_argument("--levels", type=int, default=0,
                     help="eviction levels per insert pass (0: the library default, 12)")
+    ap.add_argument("--level-stop", type=int, default=0,
+                    help="fewest chains a level runs with (0: the library default, 2^18)")
     ap.add_argument("--slice-bytes", type=int, default=0,
                     help="table bytes per slice (0: the library default, 32 MiB)")
     ap.add_argument("--slice-chunk", type=int, default=0,
