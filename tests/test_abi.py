@@ -74,3 +74,8 @@ def test_host_side_validation_without_gpu(lib):
     assert L.cf_create_ex(ctypes.byref(CfConfig(1000, 16, 4, 0, 0, 0, 0)),
                           ctypes.byref(h)) == 1  # CF_EINVAL before any CUDA call
     assert L.cf_destroy(None) == 0
+    # Setters refuse a missing filter before touching it (CF_EINVAL).
+    assert L.cf_set_eviction_levels(None, 1, 0, 0, 0) == 1
+    assert L.cf_set_host_reads(None, 0) == 1
+    assert L.cf_set_eviction_map(None, 1, 0) == 1
+    assert L.cf_version() >= 10200
