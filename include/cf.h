@@ -296,10 +296,13 @@ cf_status cf_set_eviction_map(cf_filter* f, int mode, uint64_t min_queue);
  * chains (0: 2^18), the remaining chains run to their end as in the loop.
  * The library allocates two record buffers of about 12 bytes per key of a
  * pass each on first use (freed by cf_destroy, or here when n_levels
- * changes); if that allocation fails, the insert runs the loop instead.  mode: 0 off; 1 (the default) for inserts of device buffers
- * only: beside the host-buffer calls' copies the levels slow those copies
- * more than they save (measured: 15-45% more copy time per step of the
- * large workload), so those calls keep the loop; 2 for every sliced insert.
+ * changes); if that allocation fails, the insert runs the loop instead.
+ * mode: 0 off; 1 (the default) for inserts of device buffers into filters
+ * with buckets of at most 8 bytes: beside the host-buffer calls' copies
+ * the levels slow those copies more than they save (measured: 15-45% more
+ * copy time per step of the large workload), and with wider buckets they
+ * measured slower than the loop (f16 b16 fill to LF 0.95 on 2^28 slots:
+ * 21.7 against 23.9 G inserts/s); 2 for every sliced insert.
  * CF_EINVAL for a bad mode or n_levels > 256.  Waits for the filter's
  * queued work; takes effect with the next insert call. */
 cf_status cf_set_eviction_levels(cf_filter* f, int mode, uint32_t n_levels,

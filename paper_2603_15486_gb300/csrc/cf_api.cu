@@ -82,6 +82,10 @@ uint32_t victim_cap(const cf_config* c) {
   return c->victim_capacity ? c->victim_capacity : kDefaultVictims;
 }
 
+uint64_t bucket_bytes(const cf_config* c) {
+  return uint64_t(c->slots_per_bucket) * c->fp_bits / 8;
+}
+
 size_t table_bytes(const cf_config* c) {
   return size_t(c->num_buckets) * c->slots_per_bucket * c->fp_bits / 8;
 }
@@ -507,7 +511,11 @@ cf_status run_sliced(cf_filter* f, Op op, const uint64_t* keys, uint64_t n,
   if (op == OP_INSERT) {
     st = ensure_queue(f, chunk, kSliceChunkMax);
     if (st != CF_OK) return st;
-    st = evict_map_for(f, &em, f->lv_mode != 0 ? chunk : 0);
+    // Automatic mode: buckets of up to 8 bytes (with wider buckets the
+    // levels measured slower than the loop: f16 b16 fill to LF 0.95 on
+    // 2^28 slots 21.7 against 23.9 G inserts/s).
+    const bool lv = f->lv_mode == 2 || (f->lv_mode == 1 && bucket_bytes(&f->cfg) <= 8);
+    st = evict_map_for(f, &em, lv ? chunk : 0);
     if (st != CF_OK) return st;
   }
   for (uint64_t off = 0; off < n; off += chunk) {

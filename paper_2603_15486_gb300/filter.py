@@ -226,9 +226,9 @@ class CuckooFilter:
     def set_eviction_levels(self, mode: str = "on", n_levels: int = 0, min_queue: int = 0,
                             stop_queue: int = 0):
         """Slice-grouped eviction levels of the sliced insert
-        (cf_set_eviction_levels): "off", "on" (device-buffer inserts; the
-        default) or "always" (host-buffer inserts too); 0 takes the library
-        defaults."""
+        (cf_set_eviction_levels): "off", "on" (device-buffer inserts into
+        filters with buckets of at most 8 bytes; the default) or "always"
+        (every sliced insert); 0 takes the library defaults."""
         code = {"off": 0, "on": 1, "always": 2}[mode]
         check(self._L.cf_set_eviction_levels(self._h, code, int(n_levels), int(min_queue),
                                              int(stop_queue)),

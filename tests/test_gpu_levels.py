@@ -16,8 +16,9 @@ asked of the full-bucket map).  So:
   * a batch skewed into one slice overflows a level's buffer: those chains
     run to their end at once, and the invariants still hold;
   * the levels run only when switched on, for BFS, with the map, and for
-    queues of at least min_queue keys; host-buffer inserts take them only
-    in the "always" mode.
+    queues of at least min_queue keys; host-buffer inserts and filters
+    with buckets wider than 8 bytes take them only in the "always" mode
+    (the tests below use that mode to cover every geometry).
 """
 import numpy as np
 import pytest
@@ -43,7 +44,7 @@ def _levels_filter(cf, m, f, b, policy="xor", n_levels=24, stop_queue=1, max_ev=
     g = cf.CuckooFilter(m, f, b, max_ev, policy=policy, victim_capacity=victim_capacity)
     g.set_eviction_map("always")
     g.set_slicing("always", 1024)
-    g.set_eviction_levels("on", n_levels, 1, stop_queue)
+    g.set_eviction_levels("always", n_levels, 1, stop_queue)
     g.set_kernel_timing(True)
     return g
 
@@ -189,6 +190,22 @@ def test_levels_rules(cf):
         g.set_eviction_levels("bogus")
     with pytest.raises(Exception):
         g.set_eviction_levels("on", 257)
+
+
+def test_automatic_levels_only_for_narrow_buckets(cf):
+    """The default mode takes the levels for buckets of up to 8 bytes, not
+    for wider ones (where they measured slower than the loop); "always"
+    takes them for both."""
+    for (f, b), mode, runs in (((16, 4), "on", True), ((16, 16), "on", False),
+                               ((16, 16), "always", True)):
+        m = 1 << 10 if b == 16 else 1 << 12
+        ks = workloads.keys(911 + b, int(0.96 * m * b))
+        o = oracle.OracleFilter(m, f, b, 500)
+        g = _levels_filter(cf, m, f, b)
+        g.set_eviction_levels(mode, 0, 1, 1)
+        flags = g.insert(to_dev(ks)).cpu().numpy()
+        st = _check(cf, g, o, ks, flags, "xor", m, f, b)
+        assert (st["level_passes"] > 0) == runs, (f, b, mode)
 
 
 @pytest.mark.parametrize("mode,runs", [("on", False), ("always", True)])
